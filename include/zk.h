@@ -1,0 +1,142 @@
+/*
+ * zk.h - C ABI of the B300 Zakharov / HOS wave step.
+ *
+ * The library advances the canonical Zakharov pair (eta, psi) of
+ * "Hamiltonian Two-Way Coupling of Nonlinear Waves and 3D Flows"
+ * (Sec. 3.1, Eqs. 4-5) on a doubly periodic grid over finite depth h. The
+ * Dirichlet-Neumann operator G(eta) is the order-M truncated series of
+ * Sec. 3.2 (Eq. 9; M = number of retained terms G_0 .. G_{M-1}, so the
+ * paper's HOS-3 is M = 3), evaluated with the 3/2-rule de-aliasing and the
+ * super-Gaussian taper of Sec. 6.1, the nonlinear Bernoulli term of
+ * Eqs. 10-11, the state filter of Eq. 17, and classical RK4 or the
+ * integrating-factor AB2 of Sec. 3.4 (Eqs. 15-16) as time integrator.
+ *
+ * Conventions shared by every entry point
+ *  - Physical arrays are row-major [nz][nx], x fastest, element (iz, ix) at
+ *    x = ix * Lx/nx, z = iz * Lz/nz. Their element type is given by a dtype
+ *    argument (ZK_F32 or ZK_F64), independent of the context's compute
+ *    precision; on_device = 1 means the pointer is device memory of the
+ *    context's current device, 0 means host memory (pageable or pinned).
+ *  - The caller owns every buffer it passes; the library copies inputs in and
+ *    results out and keeps no pointer after the call returns.
+ *  - The context owns all device memory it uses (allocated in zk_create,
+ *    freed in zk_destroy) and launches on the stream given in zk_options
+ *    (NULL = the legacy default stream).
+ *  - Functions return a zk_status and never abort. A CUDA error seen during a
+ *    call is returned as ZK_ECUDA; an asynchronous device error is reported
+ *    by the next call that synchronises (zk_sync, zk_get_state, zk_energy).
+ *  - A context is used by one host thread at a time.
+ */
+#ifndef ZK_H
+#define ZK_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct zk_ctx zk_ctx;
+
+typedef enum {
+    ZK_OK = 0,
+    ZK_EINVAL = 1,        /* bad argument (size, pointer, dtype, option value) */
+    ZK_ENOMEM = 2,        /* device or host allocation failed */
+    ZK_ECUDA = 3,         /* a CUDA runtime call or kernel launch failed */
+    ZK_ENONFINITE = 4,    /* the state holds NaN or Inf (checked by zk_energy) */
+    ZK_ETIMEOUT = 5,      /* a bounded device-side wait ran out */
+    ZK_EUNSUPPORTED = 6,  /* valid request this build does not implement */
+    ZK_ESTATE = 7         /* call out of order (e.g. step before set_state) */
+} zk_status;
+
+enum { ZK_F32 = 0, ZK_F64 = 1 };               /* element types of I/O arrays and of the compute path */
+enum { ZK_RK4 = 0, ZK_IFAB2 = 1 };             /* time integrators */
+
+typedef struct {
+    double eps;        /* nonlinear-amplitude parameter of Eqs. 9-11, in [0, 1]; default 1 */
+    int integrator;    /* ZK_RK4 (default) or ZK_IFAB2 (Sec. 3.4, Eqs. 15-16) */
+    int taper;         /* 1 (default): taper exp[-(|k|/kc)^8] on nonlinear products (Sec. 6.1) */
+    int filter;        /* 1 (default): state filter A(k) of Eq. 17 once per step */
+    void *stream;      /* cudaStream_t for all launches; NULL = legacy default stream */
+} zk_options;
+
+/* Create a context for an nx x nz grid of extent Lx x Lz over depth h, gravity g,
+ * with M retained DNO terms (1 <= M <= ZK_MAX_ORDER) and compute precision
+ * ZK_F32 or ZK_F64. nx, nz: powers of two in [16, 2048] (FP64: [16, 1024]).
+ * Allocates all device buffers on the current device. Options start at their
+ * defaults. Errors: ZK_EINVAL (sizes, M, precision, non-positive lengths),
+ * ZK_ENOMEM, ZK_ECUDA. *out is NULL on error. */
+#define ZK_MAX_ORDER 8
+zk_status zk_create(zk_ctx **out, int nx, int nz, double Lx, double Lz,
+                    double h, double g, int M, int precision);
+
+/* Release every device buffer and the context (NULL is accepted). */
+void zk_destroy(zk_ctx *ctx);
+
+/* Replace the options (copied). ZK_EINVAL if eps is outside [0, 1] or a flag is unknown. */
+zk_status zk_set_options(zk_ctx *ctx, const zk_options *opt);
+zk_status zk_get_options(const zk_ctx *ctx, zk_options *opt);
+
+/* Load the state from physical eta, psi [nz][nx]. The library forms their
+ * spectra and sets the Nyquist mode of each axis to zero (the paper does not
+ * say; this is the reading every spectral operator here uses). Resets the
+ * integrator history (the next IF-AB2 step bootstraps with IF-Euler). */
+zk_status zk_set_state(zk_ctx *ctx, const void *eta, const void *psi, int dtype, int on_device);
+
+/* Copy the current state out as physical eta, psi [nz][nx]. Synchronises. */
+zk_status zk_get_state(zk_ctx *ctx, void *eta, void *psi, int dtype, int on_device);
+
+/* Right-hand side of Eqs. 4 and 10 at the current state, as physical fields
+ * [nz][nx]: d eta/dt = G(eta) psi (mean set to zero), d psi/dt. Synchronises. */
+zk_status zk_rhs(zk_ctx *ctx, void *deta_dt, void *dpsi_dt, int dtype, int on_device);
+
+/* Forward DNO map of Eq. 18, v = G(eta) psi with M terms, physical [nz][nx]
+ * (mean set to zero). Synchronises. */
+zk_status zk_dno(zk_ctx *ctx, void *v, int dtype, int on_device);
+
+/* Advance n steps of size dt with the selected integrator (each followed by
+ * the state filter when enabled). Asynchronous on the context's stream; the
+ * launch sequence of one step is captured once in a CUDA graph and replayed.
+ * ZK_ESTATE before zk_set_state. */
+zk_status zk_step(zk_ctx *ctx, double dt, int n);
+
+/* Hamiltonian of Eq. 1 by Parseval, reduced in FP64 on the device in a fixed
+ * order: H = kin + pot, kin = 1/2 int psi G(eta) psi, pot = 1/2 g int eta^2,
+ * mean_eta = spatial mean of eta. Any pointer may be NULL. Synchronises.
+ * ZK_ENONFINITE if the state holds NaN/Inf. */
+zk_status zk_energy(zk_ctx *ctx, double *H, double *kin, double *pot, double *mean_eta);
+
+/* Wait for all work of the context; returns a pending asynchronous error. */
+zk_status zk_sync(zk_ctx *ctx);
+
+/* Bytes of device memory the context holds. */
+zk_status zk_device_bytes(const zk_ctx *ctx, size_t *bytes);
+
+/* Number of kernel launches one zk_step(dt, 1) issues. */
+zk_status zk_launches_per_step(const zk_ctx *ctx, int *n);
+
+/* Kernel classes reported by zk_profile_step. */
+enum { ZK_K_COL_STATE = 0, ZK_K_ROW_ROUND = 1, ZK_K_COL_PHI = 2, ZK_K_ROW_FINAL = 3, ZK_K_COL_FINAL = 4 };
+
+/* Run nsteps steps of size dt eagerly (no graph) with a CUDA event recorded
+ * on the context's stream before every launch and after the last one, and
+ * add each launch's device time in milliseconds to ms[slot] (slot = launch
+ * index within one step, in launch order; ms must hold *nslots entries, at
+ * most cap). For every slot, kind[slot] is its kernel class and
+ * bytes[slot] the algorithmic global-memory bytes it must move (each input
+ * field read once, each output written once); kind and bytes may be NULL.
+ * The state advances exactly as with zk_step. Synchronises. */
+zk_status zk_profile_step(zk_ctx *ctx, double dt, int nsteps, double *ms, int *kind, double *bytes,
+                          int cap, int *nslots);
+
+/* Static text for a status code. */
+const char *zk_strerror(zk_status s);
+
+/* Library version string. */
+const char *zk_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ZK_H */

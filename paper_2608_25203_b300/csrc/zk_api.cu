@@ -1,0 +1,808 @@
+// zk_api.cu - the C ABI of include/zk.h: context, device buffers, launch order.
+//
+// One right-hand side at order M is 2M+1 launches (Sec. 3.2 recursion, one
+// de-aliased grid per evaluation, Sec. 6.1):
+//   col(kind 0) -> [row(r) -> col(kind 1, r)] for r = 1..M-1 -> row(final) -> col(final)
+// An RK4 step is four of them; the final column kernel of each stage does the
+// stage combination, and the last one also applies the state filter (Eq. 17).
+// zk_step captures the launches of one step into a CUDA graph (re-captured
+// when dt or the options change) and replays it n times on the context's
+// stream.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/zk.h"
+#include "zk_kernels.cuh"
+
+using namespace zk;
+
+namespace {
+
+constexpr int kIoElem = 8;  // bytes per staging element (fits f32 and f64)
+
+template <int NPZ> constexpr int col_cb() { return Plan<NPZ>::TL >= 64 ? 4 : (128 / Plan<NPZ>::TL); }
+
+std::mutex g_attr_mu;
+std::unordered_map<const void*, int> g_attr;
+
+cudaError_t ensure_smem(const void* fn, size_t bytes) {
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    auto it = g_attr.find(fn);
+    if (it != g_attr.end() && it->second >= (int)bytes) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) g_attr[fn] = (int)bytes;
+    return e;
+}
+
+bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+}  // namespace
+
+struct zk_ctx {
+    int nx = 0, nz = 0, npx = 0, npz = 0, hx = 0, M = 0, prec = ZK_F32;
+    double Lx = 0, Lz = 0, h = 0, g = 0;
+    zk_options opt{};
+    int device = 0;
+    bool has_state = false;
+    size_t csz = 0;  // bytes per complex element
+    void *tw_x = nullptr, *tw_z = nullptr, *tw_px = nullptr, *tw_pz = nullptr;
+    void *y_eta = nullptr, *y_psi = nullptr, *ys_eta = nullptr, *ys_psi = nullptr;
+    void *ka_eta = nullptr, *ka_psi = nullptr, *ko_eta = nullptr, *ko_psi = nullptr;
+    void *col = nullptr;
+    int nfields = 0;
+    long long fstride = 0;
+    void *acc = nullptr;
+    void *stage = nullptr;
+    double *partial = nullptr;
+    int npartial = 0;
+    double *esum = nullptr;
+    size_t bytes = 0;
+    std::vector<void*> allocs;
+    // graph of one step
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    bool gvalid = false;
+    double gdt = 0.0;
+    int launches_per_step = 0;
+    // per-launch profiling (zk_profile_step): events recorded before each launch
+    std::vector<cudaEvent_t>* prof_ev = nullptr;
+    std::vector<int> slot_kind;
+    std::vector<double> slot_bytes;
+};
+
+namespace {
+
+cudaStream_t user_stream(const zk_ctx* c) { return (cudaStream_t)c->opt.stream; }
+
+zk_status cu(cudaError_t e) { return e == cudaSuccess ? ZK_OK : ZK_ECUDA; }
+
+// Column-space field indices.
+struct Fields {
+    int M;
+    int eta() const { return 0; }
+    int dzeta() const { return 1; }
+    int psi() const { return 2; }
+    int dzpsi() const { return 3; }
+    int base(int j) const {  // first dz^a Phi(j) field, j >= 1
+        int b = 4 + M;
+        for (int r = 1; r < j; ++r) b += M - r;
+        return b;
+    }
+    int z(int j, int a) const { return j == 0 ? 3 + a : base(j) + a - 1; }
+    int phiout() const { return base(M); }
+    int gnl() const { return phiout() + 1; }
+    int npsi() const { return phiout() + 2; }
+    int count() const { return phiout() + 3; }
+};
+
+template <typename T>
+void make_twiddles(int n, std::vector<cx<T>>& out) {
+    out.resize(n);
+    for (int t = 0; t < n; ++t) {
+        const double ang = -2.0 * M_PI * (double)t / (double)n;
+        out[t] = mk<T>((T)std::cos(ang), (T)std::sin(ang));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Launch helpers dispatched on the compile-time line lengths.
+// ---------------------------------------------------------------------------
+template <typename T, int NPX>
+cudaError_t launch_row_t(const RowArgs<T>& a, const cx<T>* tw, int npz, cudaStream_t s) {
+    constexpr int TL = Plan<NPX>::TL;
+    int nl = a.nlines;
+    if constexpr (TL < 32) { constexpr int per = 32 / TL; nl = (nl + per - 1) / per * per; }
+    const int threads = nl * TL;
+    const size_t smem = (size_t)nl * line_stride(NPX) * sizeof(cx<T>);
+    cudaError_t e = ensure_smem((const void*)row_round_kernel<T, NPX>, smem);
+    if (e != cudaSuccess) return e;
+    row_round_kernel<T, NPX><<<npz, threads, smem, s>>>(a, tw);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_row(int npx, const RowArgs<T>& a, const cx<T>* tw, int npz, cudaStream_t s) {
+    switch (npx) {
+    case 24: return launch_row_t<T, 24>(a, tw, npz, s);
+    case 48: return launch_row_t<T, 48>(a, tw, npz, s);
+    case 96: return launch_row_t<T, 96>(a, tw, npz, s);
+    case 192: return launch_row_t<T, 192>(a, tw, npz, s);
+    case 384: return launch_row_t<T, 384>(a, tw, npz, s);
+    case 768: return launch_row_t<T, 768>(a, tw, npz, s);
+    case 1536: return launch_row_t<T, 1536>(a, tw, npz, s);
+    case 3072: if constexpr (sizeof(T) == 4) return launch_row_t<T, 3072>(a, tw, npz, s); else return cudaErrorInvalidValue;
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename T, int NPZ>
+cudaError_t launch_col_t(const ColArgs<T>& a, const cx<T>* tw, cudaStream_t s, int* nblocks) {
+    constexpr int TL = Plan<NPZ>::TL;
+    constexpr int CB = col_cb<NPZ>();
+    constexpr int NZ = 2 * NPZ / 3;
+    constexpr int LS = line_stride(NPZ);
+    const int threads = CB * TL < 32 ? 32 : CB * TL;
+    const int groups = threads / TL;
+    const size_t per = (a.kind == COL_FINAL) ? (size_t)2 * LS : (size_t)(LS + NZ);
+    const size_t smem = (size_t)groups * per * sizeof(cx<T>);
+    const int grid = (a.hx + CB - 1) / CB;
+    if (nblocks) *nblocks = grid;
+    cudaError_t e = ensure_smem((const void*)col_kernel<T, NPZ, CB>, smem);
+    if (e != cudaSuccess) return e;
+    col_kernel<T, NPZ, CB><<<grid, threads, smem, s>>>(a, tw);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_col(int npz, const ColArgs<T>& a, const cx<T>* tw, cudaStream_t s, int* nblocks = nullptr) {
+    switch (npz) {
+    case 24: return launch_col_t<T, 24>(a, tw, s, nblocks);
+    case 48: return launch_col_t<T, 48>(a, tw, s, nblocks);
+    case 96: return launch_col_t<T, 96>(a, tw, s, nblocks);
+    case 192: return launch_col_t<T, 192>(a, tw, s, nblocks);
+    case 384: return launch_col_t<T, 384>(a, tw, s, nblocks);
+    case 768: return launch_col_t<T, 768>(a, tw, s, nblocks);
+    case 1536: return launch_col_t<T, 1536>(a, tw, s, nblocks);
+    case 3072: if constexpr (sizeof(T) == 4) return launch_col_t<T, 3072>(a, tw, s, nblocks); else return cudaErrorInvalidValue;
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int N> int col_blocks_for(int hx) { return (hx + col_cb<N>() - 1) / col_cb<N>(); }
+int col_grid(int npz, int hx) {
+    switch (npz) {
+    case 24: return col_blocks_for<24>(hx); case 48: return col_blocks_for<48>(hx);
+    case 96: return col_blocks_for<96>(hx); case 192: return col_blocks_for<192>(hx);
+    case 384: return col_blocks_for<384>(hx); case 768: return col_blocks_for<768>(hx);
+    case 1536: return col_blocks_for<1536>(hx); case 3072: return col_blocks_for<3072>(hx);
+    default: return 1;
+    }
+}
+
+template <typename T, typename TIN, int NX>
+cudaError_t launch_rows_fwd_t(const void* fa, const void* fb, int nz, cx<T>* oa, cx<T>* ob, const cx<T>* tw, cudaStream_t s) {
+    constexpr int TL = Plan<NX>::TL;
+    const int threads = TL >= 128 ? TL : 128;
+    const int rows = threads / TL;
+    const size_t smem = (size_t)rows * line_stride(NX) * sizeof(cx<T>);
+    cudaError_t e = ensure_smem((const void*)rows_fwd_kernel<T, TIN, NX>, smem);
+    if (e != cudaSuccess) return e;
+    rows_fwd_kernel<T, TIN, NX><<<(nz + rows - 1) / rows, threads, smem, s>>>((const TIN*)fa, (const TIN*)fb, nz, oa, ob, tw);
+    return cudaGetLastError();
+}
+template <typename T, typename TOUT, int NX>
+cudaError_t launch_rows_inv_t(const cx<T>* ia, const cx<T>* ib, int nz, T scale, void* fa, void* fb, const cx<T>* tw, cudaStream_t s) {
+    constexpr int TL = Plan<NX>::TL;
+    const int threads = TL >= 128 ? TL : 128;
+    const int rows = threads / TL;
+    const size_t smem = (size_t)rows * line_stride(NX) * sizeof(cx<T>);
+    cudaError_t e = ensure_smem((const void*)rows_inv_kernel<T, TOUT, NX>, smem);
+    if (e != cudaSuccess) return e;
+    rows_inv_kernel<T, TOUT, NX><<<(nz + rows - 1) / rows, threads, smem, s>>>(ia, ib, nz, scale, (TOUT*)fa, (TOUT*)fb, tw);
+    return cudaGetLastError();
+}
+template <typename T, int NZ, bool INV>
+cudaError_t launch_cols_t(cx<T>* f0, cx<T>* f1, int hx, const cx<T>* tw, cudaStream_t s) {
+    constexpr int TL = Plan<NZ>::TL;
+    const int threads = TL >= 128 ? TL : 128;
+    const int cols = threads / TL;
+    const size_t smem = (size_t)cols * line_stride(NZ) * sizeof(cx<T>);
+    cudaError_t e = ensure_smem((const void*)cols_kernel<T, NZ, INV>, smem);
+    if (e != cudaSuccess) return e;
+    cols_kernel<T, NZ, INV><<<(hx + cols - 1) / cols, threads, smem, s>>>(f0, f1, hx, tw);
+    return cudaGetLastError();
+}
+
+#define ZK_SWITCH_N(n, CALL)                                     \
+    switch (n) {                                                 \
+    case 16: { constexpr int N_ = 16; return CALL; }             \
+    case 32: { constexpr int N_ = 32; return CALL; }             \
+    case 64: { constexpr int N_ = 64; return CALL; }             \
+    case 128: { constexpr int N_ = 128; return CALL; }           \
+    case 256: { constexpr int N_ = 256; return CALL; }           \
+    case 512: { constexpr int N_ = 512; return CALL; }           \
+    case 1024: { constexpr int N_ = 1024; return CALL; }         \
+    case 2048: { constexpr int N_ = 2048; return CALL; }         \
+    default: return cudaErrorInvalidValue;                       \
+    }
+
+template <typename T, typename TIN>
+cudaError_t launch_rows_fwd(int nx, const void* fa, const void* fb, int nz, cx<T>* oa, cx<T>* ob, const cx<T>* tw, cudaStream_t s) {
+    ZK_SWITCH_N(nx, (launch_rows_fwd_t<T, TIN, N_>(fa, fb, nz, oa, ob, tw, s)))
+}
+template <typename T, typename TOUT>
+cudaError_t launch_rows_inv(int nx, const cx<T>* ia, const cx<T>* ib, int nz, T scale, void* fa, void* fb, const cx<T>* tw, cudaStream_t s) {
+    ZK_SWITCH_N(nx, (launch_rows_inv_t<T, TOUT, N_>(ia, ib, nz, scale, fa, fb, tw, s)))
+}
+template <typename T, bool INV>
+cudaError_t launch_cols(int nz, cx<T>* f0, cx<T>* f1, int hx, const cx<T>* tw, cudaStream_t s) {
+    ZK_SWITCH_N(nz, (launch_cols_t<T, N_, INV>(f0, f1, hx, tw, s)))
+}
+
+// ---------------------------------------------------------------------------
+// The right-hand-side pipeline.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Pipe {
+    static cx<T>* C(void* p) { return reinterpret_cast<cx<T>*>(p); }
+
+    static ColArgs<T> col_base(const zk_ctx* c) {
+        ColArgs<T> a;
+        std::memset(&a, 0, sizeof(a));
+        a.hx = c->hx;
+        a.nz_grid = c->nz;
+        a.nx_grid = c->nx;
+        a.kx0 = (T)(2.0 * M_PI / c->Lx);
+        a.kz0 = (T)(2.0 * M_PI / c->Lz);
+        a.h = (T)c->h;
+        a.g = (T)c->g;
+        const double dmax = std::max(c->Lx / c->nx, c->Lz / c->nz);
+        a.kc = (T)(2.0 / 3.0 * M_PI / dmax);
+        a.taper = c->opt.taper;
+        a.fscale = (T)((double)c->nx * c->nz / ((double)c->npx * c->npz));
+        a.iscale = (T)(1.0 / ((double)c->nx * c->nz));
+        a.colbase = C(c->col);
+        a.fstride = c->fstride;
+        a.filter = c->opt.filter;
+        return a;
+    }
+
+    static RowArgs<T> row_base(const zk_ctx* c) {
+        RowArgs<T> a;
+        std::memset(&a, 0, sizeof(a));
+        a.colbase = C(c->col);
+        a.fstride = c->fstride;
+        a.M = c->M;
+        a.eps = (T)c->opt.eps;
+        double p = 1.0;
+        for (int j = 0; j < kMaxOrder + 3; ++j) { a.epsp[j] = (T)p; p *= c->opt.eps; }
+        a.kx0 = (T)(2.0 * M_PI / c->Lx);
+        a.acc = reinterpret_cast<T*>(c->acc);
+        a.s_eta = a.s_etax = a.s_etaz = a.s_psix = a.s_psiz = a.s_g0psi = a.s_F0 = -1;
+        for (int l = 0; l < kMaxLines; ++l) { a.fa[l] = -1; a.fb[l] = -1; }
+        return a;
+    }
+
+    // slot list helper: appends a real field (field index, dx flag) and returns its slot
+    struct Slots {
+        RowArgs<T>* a;
+        int n = 0;
+        int add(int f, bool dx) {
+            const int l = n >> 1;
+            if (n & 1) { a->fb[l] = f; if (dx) a->dxb |= 1u << l; }
+            else { a->fa[l] = f; if (dx) a->dxa |= 1u << l; }
+            return n++;
+        }
+        void finish() { a->nlines = (n + 1) >> 1; }
+    };
+
+    // Enqueue one right-hand side at state (se, sp); the final column kernel
+    // runs `mode` with the given epilogue arguments already in `fin`.
+    // Record the profiling event of the next launch, with its class and its
+    // algorithmic bytes (each input field read once, each output written once).
+    static void note(zk_ctx* c, cudaStream_t s, int kind, double bytes) {
+        if (!c->prof_ev) return;
+        cudaEvent_t ev;
+        cudaEventCreate(&ev);
+        cudaEventRecord(ev, s);
+        c->prof_ev->push_back(ev);
+        c->slot_kind.push_back(kind);
+        c->slot_bytes.push_back(bytes);
+    }
+
+    static cudaError_t rhs(zk_ctx* c, const cx<T>* se, const cx<T>* sp, ColArgs<T> fin, cudaStream_t s, int* nlaunch) {
+        const Fields F{c->M};
+        const int M = c->M;
+        const double U = (double)c->fstride * sizeof(cx<T>);                 // one column-space field
+        const double Cc = (double)c->nz * c->hx * sizeof(cx<T>);             // one compact spectrum
+        const double Pp = (double)c->npz * c->npx * sizeof(T);               // the padded accumulator
+        const cx<T>* twx = reinterpret_cast<const cx<T>*>(c->tw_px);
+        const cx<T>* twz = reinterpret_cast<const cx<T>*>(c->tw_pz);
+        cudaError_t e;
+        int nl = 0;
+        // round 0: state -> column space
+        {
+            ColArgs<T> a = col_base(c);
+            a.kind = COL_FROM_STATE;
+            a.st_eta = se;
+            a.st_psi = sp;
+            int o = 0;
+            auto out = [&](int f, int src, int sym, int aa) {
+                a.out_f[o] = f; a.out_src[o] = src; a.out_sym[o] = sym; a.out_a[o] = aa; ++o;
+            };
+            out(F.eta(), 0, SYM_ID, 0);
+            out(F.dzeta(), 0, SYM_DZ, 0);
+            out(F.psi(), 1, SYM_ID, 0);
+            out(F.dzpsi(), 1, SYM_DZ, 0);
+            for (int q = 1; q <= M; ++q) out(F.z(0, q), 1, SYM_ZA, q);
+            a.nout = o;
+            note(c, s, ZK_K_COL_STATE, 2 * Cc + o * U);
+            if ((e = launch_col<T>(c->npz, a, twz, s)) != cudaSuccess) return e;
+            ++nl;
+        }
+        for (int r = 1; r <= M - 1; ++r) {
+            RowArgs<T> ra = row_base(c);
+            ra.kind = 0;
+            ra.r = r;
+            Slots sl{&ra};
+            ra.s_eta = sl.add(F.eta(), false);
+            if (r >= 2 && r - 1 <= M - 3) {
+                ra.s_etax = sl.add(F.eta(), true);
+                ra.s_etaz = sl.add(F.dzeta(), false);
+            }
+            ra.s_F0 = sl.n;
+            for (int j = 0; j < r; ++j) sl.add(F.z(j, r - j), false);
+            sl.finish();
+            ra.out0 = C(c->col) + (long long)F.phiout() * c->fstride;
+            {
+                const bool g2 = r >= 2 && r - 1 <= M - 3;
+                const double rd = (1 + (g2 ? 1 : 0) + r) * U + (r >= 3 ? Pp : 0.0);
+                const double wr = U + (r >= 2 ? Pp : 0.0);
+                note(c, s, ZK_K_ROW_ROUND, rd + wr);
+            }
+            if ((e = launch_row<T>(c->npx, ra, twx, c->npz, s)) != cudaSuccess) return e;
+            ++nl;
+            ColArgs<T> a = col_base(c);
+            a.kind = COL_PHI;
+            a.pin = C(c->col) + (long long)F.phiout() * c->fstride;
+            int o = 0;
+            for (int q = 1; q <= M - r; ++q) {
+                a.out_f[o] = F.z(r, q); a.out_src[o] = 0; a.out_sym[o] = SYM_ZA; a.out_a[o] = q; ++o;
+            }
+            a.nout = o;
+            note(c, s, ZK_K_COL_PHI, (1 + o) * U);
+            if ((e = launch_col<T>(c->npz, a, twz, s)) != cudaSuccess) return e;
+            ++nl;
+        }
+        {
+            RowArgs<T> ra = row_base(c);
+            ra.kind = 1;
+            ra.r = M;
+            Slots sl{&ra};
+            if (M >= 2) ra.s_eta = sl.add(F.eta(), false);
+            ra.s_etax = sl.add(F.eta(), true);
+            ra.s_etaz = sl.add(F.dzeta(), false);
+            ra.s_psix = sl.add(F.psi(), true);
+            ra.s_psiz = sl.add(F.dzpsi(), false);
+            ra.s_g0psi = sl.add(F.z(0, 1), false);
+            if (M >= 2) {
+                ra.s_F0 = sl.n;
+                for (int j = 0; j < M; ++j) sl.add(F.z(j, M - j), false);
+            }
+            sl.finish();
+            ra.out0 = C(c->col) + (long long)F.gnl() * c->fstride;
+            ra.out1 = C(c->col) + (long long)F.npsi() * c->fstride;
+            note(c, s, ZK_K_ROW_FINAL, (5 + (M >= 2 ? M : 0) + 2) * U + (M >= 3 ? Pp : 0.0));
+            if ((e = launch_row<T>(c->npx, ra, twx, c->npz, s)) != cudaSuccess) return e;
+            ++nl;
+        }
+        {
+            fin.kind = COL_FINAL;
+            fin.gin = C(c->col) + (long long)F.gnl() * c->fstride;
+            fin.nin = C(c->col) + (long long)F.npsi() * c->fstride;
+            fin.s_eta = se;
+            fin.s_psi = sp;
+            {
+                // 2 products in, the stage state, then the epilogue's own traffic
+                double b = 2 * U + 2 * Cc;
+                switch (fin.mode) {
+                case FIN_RHS: b += 2 * Cc; break;
+                case FIN_RK1: b += 4 * Cc; break;                 // ka, ys written (state is y)
+                case FIN_RK2: case FIN_RK3: b += 8 * Cc; break;   // y, ka read; ka, ys written
+                case FIN_RK4: b += 6 * Cc; break;                 // y, ka read; y written
+                default: break;
+                }
+                note(c, s, ZK_K_COL_FINAL, b);
+            }
+            if ((e = launch_col<T>(c->npz, fin, twz, s)) != cudaSuccess) return e;
+            ++nl;
+        }
+        if (nlaunch) *nlaunch += nl;
+        return cudaSuccess;
+    }
+
+    static cudaError_t rk4_step(zk_ctx* c, double dt, cudaStream_t s, int* nlaunch) {
+        for (int st = 1; st <= 4; ++st) {
+            ColArgs<T> fin = col_base(c);
+            fin.mode = st;
+            fin.dt = (T)dt;
+            fin.y_eta = C(c->y_eta); fin.y_psi = C(c->y_psi);
+            fin.ys_eta = C(c->ys_eta); fin.ys_psi = C(c->ys_psi);
+            fin.ka_eta = C(c->ka_eta); fin.ka_psi = C(c->ka_psi);
+            const cx<T>* se = st == 1 ? C(c->y_eta) : C(c->ys_eta);
+            const cx<T>* sp = st == 1 ? C(c->y_psi) : C(c->ys_psi);
+            cudaError_t e = rhs(c, se, sp, fin, s, nlaunch);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
+
+    static cudaError_t rhs_out(zk_ctx* c, cudaStream_t s) {
+        ColArgs<T> fin = col_base(c);
+        fin.mode = FIN_RHS;
+        fin.ko_eta = C(c->ko_eta);
+        fin.ko_psi = C(c->ko_psi);
+        return rhs(c, C(c->y_eta), C(c->y_psi), fin, s, nullptr);
+    }
+
+    static cudaError_t energy(zk_ctx* c, cudaStream_t s) {
+        ColArgs<T> fin = col_base(c);
+        fin.mode = FIN_ENERGY;
+        fin.partial = c->partial;
+        cudaError_t e = rhs(c, C(c->y_eta), C(c->y_psi), fin, s, nullptr);
+        if (e != cudaSuccess) return e;
+        energy_finalize_kernel<<<1, 32, 0, s>>>(c->partial, col_grid(c->npz, c->hx), c->esum);
+        return cudaGetLastError();
+    }
+
+    // physical [nz][nx] (dtype, device pointer) -> compact state y
+    static cudaError_t set_state(zk_ctx* c, const void* de, const void* dp, int dtype, cudaStream_t s) {
+        const cx<T>* twx = reinterpret_cast<const cx<T>*>(c->tw_x);
+        const cx<T>* twz = reinterpret_cast<const cx<T>*>(c->tw_z);
+        cudaError_t e = dtype == ZK_F32
+            ? launch_rows_fwd<T, float>(c->nx, de, dp, c->nz, C(c->y_eta), C(c->y_psi), twx, s)
+            : launch_rows_fwd<T, double>(c->nx, de, dp, c->nz, C(c->y_eta), C(c->y_psi), twx, s);
+        if (e != cudaSuccess) return e;
+        return launch_cols<T, false>(c->nz, C(c->y_eta), C(c->y_psi), c->hx, twz, s);
+    }
+
+    // compact (a, b) -> physical (dtype, device pointers); a, b are overwritten
+    static cudaError_t to_physical(zk_ctx* c, cx<T>* a, cx<T>* b, void* oa, void* ob, int dtype, cudaStream_t s) {
+        const cx<T>* twx = reinterpret_cast<const cx<T>*>(c->tw_x);
+        const cx<T>* twz = reinterpret_cast<const cx<T>*>(c->tw_z);
+        cudaError_t e = launch_cols<T, true>(c->nz, a, b, c->hx, twz, s);
+        if (e != cudaSuccess) return e;
+        const T scale = (T)(1.0 / ((double)c->nx * c->nz));
+        return dtype == ZK_F32
+            ? launch_rows_inv<T, float>(c->nx, a, b, c->nz, scale, oa, ob, twx, s)
+            : launch_rows_inv<T, double>(c->nx, a, b, c->nz, scale, oa, ob, twx, s);
+    }
+};
+
+template <typename T>
+zk_status alloc_twiddles(zk_ctx* c) {
+    int ns[4] = {c->nx, c->nz, c->npx, c->npz};
+    void** dst[4] = {&c->tw_x, &c->tw_z, &c->tw_px, &c->tw_pz};
+    for (int i = 0; i < 4; ++i) {
+        std::vector<cx<T>> h;
+        make_twiddles<T>(ns[i], h);
+        void* p = nullptr;
+        if (cudaMalloc(&p, h.size() * sizeof(cx<T>)) != cudaSuccess) return ZK_ENOMEM;
+        c->allocs.push_back(p);
+        c->bytes += h.size() * sizeof(cx<T>);
+        if (cudaMemcpy(p, h.data(), h.size() * sizeof(cx<T>), cudaMemcpyHostToDevice) != cudaSuccess) return ZK_ECUDA;
+        *dst[i] = p;
+    }
+    return ZK_OK;
+}
+
+zk_status dalloc(zk_ctx* c, void** p, size_t bytes) {
+    if (cudaMalloc(p, bytes) != cudaSuccess) { *p = nullptr; cudaGetLastError(); return ZK_ENOMEM; }
+    c->allocs.push_back(*p);
+    c->bytes += bytes;
+    if (cudaMemset(*p, 0, bytes) != cudaSuccess) return ZK_ECUDA;
+    return ZK_OK;
+}
+
+void drop_graph(zk_ctx* c) {
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+    c->gvalid = false;
+}
+
+template <typename T>
+cudaError_t enqueue_step(zk_ctx* c, double dt, cudaStream_t s, int* nl) {
+    return Pipe<T>::rk4_step(c, dt, s, nl);
+}
+
+cudaError_t enqueue_step_any(zk_ctx* c, double dt, cudaStream_t s, int* nl) {
+    return c->prec == ZK_F32 ? enqueue_step<float>(c, dt, s, nl) : enqueue_step<double>(c, dt, s, nl);
+}
+
+zk_status build_graph(zk_ctx* c, double dt) {
+    drop_graph(c);
+    if (!c->cap) {
+        if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) return ZK_ECUDA;
+    }
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeRelaxed) != cudaSuccess) return ZK_ECUDA;
+    int nl = 0;
+    cudaError_t e = enqueue_step_any(c, dt, c->cap, &nl);
+    cudaError_t e2 = cudaStreamEndCapture(c->cap, &graph);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return ZK_ECUDA;
+    }
+    e = cudaGraphInstantiate(&c->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) { c->gexec = nullptr; return ZK_ECUDA; }
+    c->gvalid = true;
+    c->gdt = dt;
+    c->launches_per_step = nl;
+    return ZK_OK;
+}
+
+// Copy helpers between caller buffers and the staging area.
+zk_status stage_in(zk_ctx* c, const void* a, const void* b, int dtype, int on_device, const void** da, const void** db) {
+    const size_t n = (size_t)c->nx * c->nz * (dtype == ZK_F32 ? 4 : 8);
+    if (on_device) { *da = a; *db = b; return ZK_OK; }
+    char* st = (char*)c->stage;
+    cudaStream_t s = user_stream(c);
+    if (cudaMemcpyAsync(st, a, n, cudaMemcpyHostToDevice, s) != cudaSuccess) return ZK_ECUDA;
+    if (cudaMemcpyAsync(st + (size_t)c->nx * c->nz * kIoElem, b, n, cudaMemcpyHostToDevice, s) != cudaSuccess) return ZK_ECUDA;
+    *da = st;
+    *db = st + (size_t)c->nx * c->nz * kIoElem;
+    return ZK_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+const char* zk_strerror(zk_status s) {
+    switch (s) {
+    case ZK_OK: return "ok";
+    case ZK_EINVAL: return "invalid argument";
+    case ZK_ENOMEM: return "out of memory";
+    case ZK_ECUDA: return "CUDA error";
+    case ZK_ENONFINITE: return "state is not finite";
+    case ZK_ETIMEOUT: return "device wait timed out";
+    case ZK_EUNSUPPORTED: return "unsupported";
+    case ZK_ESTATE: return "call out of order";
+    default: return "unknown status";
+    }
+}
+
+const char* zk_version(void) { return "zk 0.1 sm_103a"; }
+
+void zk_destroy(zk_ctx* c) {
+    if (!c) return;
+    drop_graph(c);
+    if (c->cap) cudaStreamDestroy(c->cap);
+    for (void* p : c->allocs) cudaFree(p);
+    delete c;
+}
+
+zk_status zk_create(zk_ctx** out, int nx, int nz, double Lx, double Lz, double h, double g, int M, int precision) {
+    if (!out) return ZK_EINVAL;
+    *out = nullptr;
+    if (!is_pow2(nx) || !is_pow2(nz) || nx < 16 || nz < 16) return ZK_EINVAL;
+    const int nmax = precision == ZK_F64 ? 1024 : 2048;
+    if (nx > nmax || nz > nmax) return ZK_EINVAL;
+    if (!(Lx > 0) || !(Lz > 0) || !(h > 0) || !(g > 0)) return ZK_EINVAL;
+    if (M < 1 || M > ZK_MAX_ORDER) return ZK_EINVAL;
+    if (precision != ZK_F32 && precision != ZK_F64) return ZK_EINVAL;
+    zk_ctx* c = new (std::nothrow) zk_ctx();
+    if (!c) return ZK_ENOMEM;
+    c->nx = nx; c->nz = nz; c->npx = 3 * nx / 2; c->npz = 3 * nz / 2; c->hx = nx / 2;
+    c->Lx = Lx; c->Lz = Lz; c->h = h; c->g = g; c->M = M; c->prec = precision;
+    c->opt.eps = 1.0; c->opt.integrator = ZK_RK4; c->opt.taper = 1; c->opt.filter = 1; c->opt.stream = nullptr;
+    cudaGetDevice(&c->device);
+    c->csz = precision == ZK_F32 ? 8 : 16;
+    const size_t rsz = precision == ZK_F32 ? 4 : 8;
+    zk_status st = precision == ZK_F32 ? alloc_twiddles<float>(c) : alloc_twiddles<double>(c);
+    const size_t compact = (size_t)nz * c->hx * c->csz;
+    void** comp[8] = {&c->y_eta, &c->y_psi, &c->ys_eta, &c->ys_psi, &c->ka_eta, &c->ka_psi, &c->ko_eta, &c->ko_psi};
+    for (int i = 0; i < 8 && st == ZK_OK; ++i) st = dalloc(c, comp[i], compact);
+    const Fields F{M};
+    c->nfields = F.count();
+    c->fstride = (long long)c->npz * c->hx;
+    if (st == ZK_OK) st = dalloc(c, &c->col, (size_t)c->nfields * c->fstride * c->csz);
+    if (st == ZK_OK) st = dalloc(c, &c->acc, (size_t)c->npz * c->npx * rsz);
+    if (st == ZK_OK) st = dalloc(c, &c->stage, (size_t)2 * nx * nz * kIoElem);
+    c->npartial = col_grid(c->npz, c->hx);
+    if (st == ZK_OK) st = dalloc(c, (void**)&c->partial, (size_t)3 * c->npartial * sizeof(double));
+    if (st == ZK_OK) st = dalloc(c, (void**)&c->esum, 4 * sizeof(double));
+    if (st != ZK_OK) { zk_destroy(c); return st; }
+    *out = c;
+    return ZK_OK;
+}
+
+zk_status zk_set_options(zk_ctx* c, const zk_options* o) {
+    if (!c || !o) return ZK_EINVAL;
+    if (!(o->eps >= 0.0 && o->eps <= 1.0)) return ZK_EINVAL;
+    if (o->integrator != ZK_RK4 && o->integrator != ZK_IFAB2) return ZK_EINVAL;
+    if ((o->taper != 0 && o->taper != 1) || (o->filter != 0 && o->filter != 1)) return ZK_EINVAL;
+    if (o->integrator == ZK_IFAB2) return ZK_EUNSUPPORTED;
+    c->opt = *o;
+    drop_graph(c);
+    return ZK_OK;
+}
+
+zk_status zk_get_options(const zk_ctx* c, zk_options* o) {
+    if (!c || !o) return ZK_EINVAL;
+    *o = c->opt;
+    return ZK_OK;
+}
+
+zk_status zk_set_state(zk_ctx* c, const void* eta, const void* psi, int dtype, int on_device) {
+    if (!c || !eta || !psi || (dtype != ZK_F32 && dtype != ZK_F64)) return ZK_EINVAL;
+    const void *de, *dp;
+    zk_status st = stage_in(c, eta, psi, dtype, on_device, &de, &dp);
+    if (st != ZK_OK) return st;
+    cudaError_t e = c->prec == ZK_F32 ? Pipe<float>::set_state(c, de, dp, dtype, user_stream(c))
+                                      : Pipe<double>::set_state(c, de, dp, dtype, user_stream(c));
+    if (e != cudaSuccess) return ZK_ECUDA;
+    c->has_state = true;
+    return ZK_OK;
+}
+
+static zk_status out_physical(zk_ctx* c, void* ca, void* cb, void* oa, void* ob, int dtype, int on_device) {
+    cudaStream_t s = user_stream(c);
+    const size_t n = (size_t)c->nx * c->nz * (dtype == ZK_F32 ? 4 : 8);
+    char* st = (char*)c->stage;
+    void* da = on_device ? oa : (void*)st;
+    void* db = ob ? (on_device ? ob : (void*)(st + (size_t)c->nx * c->nz * kIoElem)) : nullptr;
+    cudaError_t e = c->prec == ZK_F32
+        ? Pipe<float>::to_physical(c, (cx<float>*)ca, (cx<float>*)cb, da, db, dtype, s)
+        : Pipe<double>::to_physical(c, (cx<double>*)ca, (cx<double>*)cb, da, db, dtype, s);
+    if (e != cudaSuccess) return ZK_ECUDA;
+    if (!on_device) {
+        if (cudaMemcpyAsync(oa, da, n, cudaMemcpyDeviceToHost, s) != cudaSuccess) return ZK_ECUDA;
+        if (ob && cudaMemcpyAsync(ob, db, n, cudaMemcpyDeviceToHost, s) != cudaSuccess) return ZK_ECUDA;
+    }
+    return cu(cudaStreamSynchronize(s));
+}
+
+zk_status zk_get_state(zk_ctx* c, void* eta, void* psi, int dtype, int on_device) {
+    if (!c || !eta || (dtype != ZK_F32 && dtype != ZK_F64)) return ZK_EINVAL;
+    if (!c->has_state) return ZK_ESTATE;
+    cudaStream_t s = user_stream(c);
+    const size_t compact = (size_t)c->nz * c->hx * c->csz;
+    if (cudaMemcpyAsync(c->ko_eta, c->y_eta, compact, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return ZK_ECUDA;
+    if (cudaMemcpyAsync(c->ko_psi, c->y_psi, compact, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return ZK_ECUDA;
+    return out_physical(c, c->ko_eta, c->ko_psi, eta, psi, dtype, on_device);
+}
+
+zk_status zk_rhs(zk_ctx* c, void* deta, void* dpsi, int dtype, int on_device) {
+    if (!c || !deta || (dtype != ZK_F32 && dtype != ZK_F64)) return ZK_EINVAL;
+    if (!c->has_state) return ZK_ESTATE;
+    cudaError_t e = c->prec == ZK_F32 ? Pipe<float>::rhs_out(c, user_stream(c)) : Pipe<double>::rhs_out(c, user_stream(c));
+    if (e != cudaSuccess) return ZK_ECUDA;
+    return out_physical(c, c->ko_eta, c->ko_psi, deta, dpsi, dtype, on_device);
+}
+
+zk_status zk_dno(zk_ctx* c, void* v, int dtype, int on_device) {
+    if (!c || !v || (dtype != ZK_F32 && dtype != ZK_F64)) return ZK_EINVAL;
+    if (!c->has_state) return ZK_ESTATE;
+    cudaError_t e = c->prec == ZK_F32 ? Pipe<float>::rhs_out(c, user_stream(c)) : Pipe<double>::rhs_out(c, user_stream(c));
+    if (e != cudaSuccess) return ZK_ECUDA;
+    return out_physical(c, c->ko_eta, nullptr, v, nullptr, dtype, on_device);
+}
+
+zk_status zk_step(zk_ctx* c, double dt, int n) {
+    if (!c || n < 0 || !(dt > 0) || !std::isfinite(dt)) return ZK_EINVAL;
+    if (!c->has_state) return ZK_ESTATE;
+    if (n == 0) return ZK_OK;
+    if (!c->gvalid || c->gdt != dt) {
+        zk_status st = build_graph(c, dt);
+        if (st != ZK_OK) return st;
+    }
+    cudaStream_t s = user_stream(c);
+    for (int i = 0; i < n; ++i)
+        if (cudaGraphLaunch(c->gexec, s) != cudaSuccess) return ZK_ECUDA;
+    return ZK_OK;
+}
+
+zk_status zk_energy(zk_ctx* c, double* H, double* kin, double* pot, double* mean_eta) {
+    if (!c) return ZK_EINVAL;
+    if (!c->has_state) return ZK_ESTATE;
+    cudaStream_t s = user_stream(c);
+    cudaError_t e = c->prec == ZK_F32 ? Pipe<float>::energy(c, s) : Pipe<double>::energy(c, s);
+    if (e != cudaSuccess) return ZK_ECUDA;
+    double hs[3];
+    if (cudaMemcpyAsync(hs, c->esum, sizeof(hs), cudaMemcpyDeviceToHost, s) != cudaSuccess) return ZK_ECUDA;
+    double m0[2] = {0, 0};
+    if (c->prec == ZK_F32) {
+        float2 v;
+        if (cudaMemcpyAsync(&v, c->y_eta, sizeof(v), cudaMemcpyDeviceToHost, s) != cudaSuccess) return ZK_ECUDA;
+        if (cudaStreamSynchronize(s) != cudaSuccess) return ZK_ECUDA;
+        m0[0] = v.x;
+    } else {
+        double2 v;
+        if (cudaMemcpyAsync(&v, c->y_eta, sizeof(v), cudaMemcpyDeviceToHost, s) != cudaSuccess) return ZK_ECUDA;
+        if (cudaStreamSynchronize(s) != cudaSuccess) return ZK_ECUDA;
+        m0[0] = v.x;
+    }
+    const double nn = (double)c->nx * c->nz;
+    const double w = (c->Lx / c->nx) * (c->Lz / c->nz) / nn;
+    const double k = 0.5 * w * hs[0];
+    const double p = 0.5 * c->g * w * hs[1];
+    if (H) *H = k + p;
+    if (kin) *kin = k;
+    if (pot) *pot = p;
+    if (mean_eta) *mean_eta = m0[0] / nn;
+    if (hs[2] != 0.0 || !std::isfinite(k) || !std::isfinite(p)) return ZK_ENONFINITE;
+    return ZK_OK;
+}
+
+zk_status zk_profile_step(zk_ctx* c, double dt, int nsteps, double* ms, int* kind, double* bytes, int cap, int* nslots) {
+    if (!c || !ms || !nslots || nsteps < 1 || !(dt > 0)) return ZK_EINVAL;
+    if (!c->has_state) return ZK_ESTATE;
+    cudaStream_t s = user_stream(c);
+    int n0 = -1;
+    for (int i = 0; i < nsteps; ++i) {
+        std::vector<cudaEvent_t> ev;
+        c->prof_ev = &ev;
+        c->slot_kind.clear();
+        c->slot_bytes.clear();
+        int nl = 0;
+        cudaError_t e = enqueue_step_any(c, dt, s, &nl);
+        cudaEvent_t last;
+        cudaEventCreate(&last);
+        cudaEventRecord(last, s);
+        ev.push_back(last);
+        c->prof_ev = nullptr;
+        zk_status st = e == cudaSuccess ? cu(cudaStreamSynchronize(s)) : ZK_ECUDA;
+        const int n = (int)ev.size() - 1;
+        if (st == ZK_OK) {
+            if (n0 < 0) {
+                n0 = n;
+                if (n > cap) st = ZK_EINVAL;
+                else for (int k = 0; k < n; ++k) ms[k] = 0.0;
+            }
+            if (st == ZK_OK && n == n0) {
+                for (int k = 0; k < n; ++k) {
+                    float t = 0.f;
+                    cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+                    ms[k] += t;
+                    if (kind) kind[k] = c->slot_kind[k];
+                    if (bytes) bytes[k] = c->slot_bytes[k];
+                }
+            }
+        }
+        for (cudaEvent_t x : ev) cudaEventDestroy(x);
+        if (st != ZK_OK) return st;
+    }
+    *nslots = n0;
+    return ZK_OK;
+}
+
+zk_status zk_sync(zk_ctx* c) {
+    if (!c) return ZK_EINVAL;
+    return cu(cudaStreamSynchronize(user_stream(c)));
+}
+
+zk_status zk_device_bytes(const zk_ctx* c, size_t* b) {
+    if (!c || !b) return ZK_EINVAL;
+    *b = c->bytes;
+    return ZK_OK;
+}
+
+zk_status zk_launches_per_step(const zk_ctx* c, int* n) {
+    if (!c || !n) return ZK_EINVAL;
+    *n = 4 * (2 * c->M + 1);
+    return ZK_OK;
+}
+
+}  // extern "C"

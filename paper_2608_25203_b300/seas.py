@@ -122,8 +122,8 @@ def jonswap_sea(nx: int, nz: int, Lx: float, Lz: float, h: float, Hs: float, Tp:
     # Hermitian mirror (kx > 0 modes never coincide with their mirrors)
     eh[(-iz) % nz, (-ix) % nx] = np.conj(c)
     ph[(-iz) % nz, (-ix) % nx] = np.conj(-1j * (g / w) * c)
-    eta = np.fft.ifft2(eh).real
-    psi = np.fft.ifft2(ph).real
+    eta = np.ascontiguousarray(np.fft.ifft2(eh).real)
+    psi = np.ascontiguousarray(np.fft.ifft2(ph).real)
     std = float(np.sqrt(np.mean(eta ** 2)))
     scale = Hs / (4.0 * std) if std > 0 else 0.0
     eta *= scale

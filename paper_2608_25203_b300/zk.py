@@ -1,0 +1,256 @@
+"""Python binding of the zk C ABI (include/zk.h): argument marshalling only.
+
+Every function named ``zk_*`` here forwards to the C entry point of the same
+name in ``libzk.so``; ``Zakharov`` wraps a context for convenience. Arrays can
+be numpy arrays (host memory) or torch CUDA tensors (device memory, passed by
+pointer on the caller's current stream). The library must have been built for
+sm_103a; importing works without a GPU, but every call fails loudly if the
+shared library is missing - there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libzk.so")
+
+ZK_OK, ZK_EINVAL, ZK_ENOMEM, ZK_ECUDA, ZK_ENONFINITE, ZK_ETIMEOUT, ZK_EUNSUPPORTED, ZK_ESTATE = range(8)
+ZK_F32, ZK_F64 = 0, 1
+ZK_RK4, ZK_IFAB2 = 0, 1
+
+# every symbol include/zk.h declares
+EXPORTS = [
+    "zk_create", "zk_destroy", "zk_set_options", "zk_get_options", "zk_set_state", "zk_get_state",
+    "zk_rhs", "zk_dno", "zk_step", "zk_energy", "zk_sync", "zk_device_bytes",
+    "zk_launches_per_step", "zk_profile_step", "zk_strerror", "zk_version",
+]
+
+KERNEL_CLASSES = {0: "col_state", 1: "row_round", 2: "col_phi", 3: "row_final", 4: "col_final"}
+
+
+class ZkOptions(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("integrator", ctypes.c_int), ("taper", ctypes.c_int),
+                ("filter", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+class ZkError(RuntimeError):
+    def __init__(self, fn, status, msg):
+        super().__init__(f"{fn} failed: {msg} (status {status})")
+        self.status = status
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libzk.so (once). Raises if it is missing: the path has no fallback."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libzk.so not built at {path}; run __graft_entry__.build()")
+    L = ctypes.CDLL(path)
+    vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    pd = ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "zk_create": ([ctypes.POINTER(vp), i, i, d, d, d, d, i, i], i),
+        "zk_destroy": ([vp], None),
+        "zk_set_options": ([vp, ctypes.POINTER(ZkOptions)], i),
+        "zk_get_options": ([vp, ctypes.POINTER(ZkOptions)], i),
+        "zk_set_state": ([vp, vp, vp, i, i], i),
+        "zk_get_state": ([vp, vp, vp, i, i], i),
+        "zk_rhs": ([vp, vp, vp, i, i], i),
+        "zk_dno": ([vp, vp, i, i], i),
+        "zk_step": ([vp, d, i], i),
+        "zk_energy": ([vp, pd, pd, pd, pd], i),
+        "zk_sync": ([vp], i),
+        "zk_device_bytes": ([vp, ctypes.POINTER(ctypes.c_size_t)], i),
+        "zk_launches_per_step": ([vp, ctypes.POINTER(i)], i),
+        "zk_profile_step": ([vp, d, i, pd, ctypes.POINTER(i), pd, i, ctypes.POINTER(i)], i),
+        "zk_strerror": ([i], ctypes.c_char_p),
+        "zk_version": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def _check(fn: str, st: int):
+    if st != ZK_OK:
+        raise ZkError(fn, st, load().zk_strerror(st).decode())
+
+
+def _ptr(x, dtype_code):
+    """(pointer, on_device) for a numpy array or a torch tensor of the expected dtype."""
+    if isinstance(x, np.ndarray):
+        want = np.float32 if dtype_code == ZK_F32 else np.float64
+        if x.dtype != want or not x.flags["C_CONTIGUOUS"]:
+            raise ValueError(f"expected C-contiguous {want.__name__} array")
+        return x.ctypes.data, 0
+    import torch
+    if isinstance(x, torch.Tensor):
+        want = torch.float32 if dtype_code == ZK_F32 else torch.float64
+        if x.dtype != want or not x.is_contiguous():
+            raise ValueError(f"expected contiguous {want} tensor")
+        return x.data_ptr(), 1 if x.is_cuda else 0
+    raise TypeError("expected numpy array or torch tensor")
+
+
+# ---- thin wrappers with the C names -----------------------------------------
+def zk_create(nx, nz, Lx, Lz, h, g, M, precision=ZK_F32):
+    c = ctypes.c_void_p()
+    _check("zk_create", load().zk_create(ctypes.byref(c), nx, nz, Lx, Lz, h, g, M, precision))
+    return c
+
+
+def zk_destroy(ctx):
+    load().zk_destroy(ctx)
+
+
+def zk_set_options(ctx, eps=1.0, integrator=ZK_RK4, taper=1, filter=1, stream=None):
+    o = ZkOptions(eps, integrator, taper, filter, stream)
+    _check("zk_set_options", load().zk_set_options(ctx, ctypes.byref(o)))
+
+
+def zk_get_options(ctx):
+    o = ZkOptions()
+    _check("zk_get_options", load().zk_get_options(ctx, ctypes.byref(o)))
+    return o
+
+
+def zk_set_state(ctx, eta, psi, dtype=None):
+    dt = dtype if dtype is not None else _dtype_of(eta)
+    pe, de = _ptr(eta, dt)
+    pp, dp = _ptr(psi, dt)
+    if de != dp:
+        raise ValueError("eta and psi must both be host or both device arrays")
+    _check("zk_set_state", load().zk_set_state(ctx, pe, pp, dt, de))
+
+
+def zk_get_state(ctx, eta, psi, dtype=None):
+    dt = dtype if dtype is not None else _dtype_of(eta)
+    pe, de = _ptr(eta, dt)
+    pp, _ = _ptr(psi, dt)
+    _check("zk_get_state", load().zk_get_state(ctx, pe, pp, dt, de))
+
+
+def zk_rhs(ctx, deta, dpsi, dtype=None):
+    dt = dtype if dtype is not None else _dtype_of(deta)
+    pe, de = _ptr(deta, dt)
+    pp, _ = _ptr(dpsi, dt)
+    _check("zk_rhs", load().zk_rhs(ctx, pe, pp, dt, de))
+
+
+def zk_dno(ctx, v, dtype=None):
+    dt = dtype if dtype is not None else _dtype_of(v)
+    pv, dv = _ptr(v, dt)
+    _check("zk_dno", load().zk_dno(ctx, pv, dt, dv))
+
+
+def zk_step(ctx, dt, n=1):
+    _check("zk_step", load().zk_step(ctx, float(dt), int(n)))
+
+
+def zk_energy(ctx):
+    H, k, p, m = (ctypes.c_double() for _ in range(4))
+    _check("zk_energy", load().zk_energy(ctx, ctypes.byref(H), ctypes.byref(k), ctypes.byref(p), ctypes.byref(m)))
+    return H.value, k.value, p.value, m.value
+
+
+def zk_sync(ctx):
+    _check("zk_sync", load().zk_sync(ctx))
+
+
+def zk_device_bytes(ctx):
+    b = ctypes.c_size_t()
+    _check("zk_device_bytes", load().zk_device_bytes(ctx, ctypes.byref(b)))
+    return b.value
+
+
+def zk_launches_per_step(ctx):
+    n = ctypes.c_int()
+    _check("zk_launches_per_step", load().zk_launches_per_step(ctx, ctypes.byref(n)))
+    return n.value
+
+
+def zk_profile_step(ctx, dt, nsteps=1, cap=256):
+    """Per-launch device times (ms, summed over nsteps), kernel classes and algorithmic bytes."""
+    ms = (ctypes.c_double * cap)()
+    kind = (ctypes.c_int * cap)()
+    by = (ctypes.c_double * cap)()
+    n = ctypes.c_int()
+    _check("zk_profile_step", load().zk_profile_step(ctx, float(dt), int(nsteps), ms, kind, by, cap,
+                                                     ctypes.byref(n)))
+    k = n.value
+    return list(ms[:k]), [KERNEL_CLASSES[x] for x in kind[:k]], list(by[:k])
+
+
+def zk_version():
+    return load().zk_version().decode()
+
+
+def _dtype_of(x):
+    if isinstance(x, np.ndarray):
+        return ZK_F64 if x.dtype == np.float64 else ZK_F32
+    import torch
+    return ZK_F64 if x.dtype == torch.float64 else ZK_F32
+
+
+class Zakharov:
+    """One simulation context on the current CUDA device."""
+
+    def __init__(self, nx, nz, Lx, Lz, h, g=9.81, M=5, precision=ZK_F32, eps=1.0, taper=True,
+                 filter=True, stream=None):
+        self.nx, self.nz, self.M, self.precision = nx, nz, M, precision
+        self.ctx = zk_create(nx, nz, Lx, Lz, h, g, M, precision)
+        self._stream = stream
+        zk_set_options(self.ctx, eps=eps, taper=int(taper), filter=int(filter), stream=stream)
+
+    def close(self):
+        if self.ctx is not None:
+            zk_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_state(self, eta, psi):
+        if isinstance(eta, np.ndarray):
+            eta = np.ascontiguousarray(eta)
+            psi = np.ascontiguousarray(psi, dtype=eta.dtype)
+        zk_set_state(self.ctx, eta, psi)
+
+    def get_state(self, dtype=np.float64):
+        e = np.empty((self.nz, self.nx), dtype)
+        p = np.empty((self.nz, self.nx), dtype)
+        zk_get_state(self.ctx, e, p)
+        return e, p
+
+    def rhs(self, dtype=np.float64):
+        e = np.empty((self.nz, self.nx), dtype)
+        p = np.empty((self.nz, self.nx), dtype)
+        zk_rhs(self.ctx, e, p)
+        return e, p
+
+    def dno(self, dtype=np.float64):
+        v = np.empty((self.nz, self.nx), dtype)
+        zk_dno(self.ctx, v)
+        return v
+
+    def step(self, dt, n=1):
+        zk_step(self.ctx, dt, n)
+
+    def energy(self):
+        return zk_energy(self.ctx)
+
+    def sync(self):
+        zk_sync(self.ctx)
