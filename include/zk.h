@@ -129,6 +129,34 @@ enum { ZK_K_COL_STATE = 0, ZK_K_ROW_ROUND = 1, ZK_K_COL_PHI = 2, ZK_K_ROW_FINAL 
 zk_status zk_profile_step(zk_ctx *ctx, double dt, int nsteps, double *ms, int *kind, double *bytes,
                           int cap, int *nslots);
 
+/* ---- Allocation-free DNO (the paper has no counterpart; library addition) ----
+ *
+ * zk_dno_static computes the same v = G(eta) psi as zk_dno, but without a
+ * context and without allocating device memory, for callers that cannot
+ * call cudaMalloc: code embedded in a host application that owns the device
+ * memory pool (a raw cudaMalloc bypasses the pool's accounting or fails once
+ * the pool has reserved the memory), and loops with latency limits that
+ * forbid allocation after start-up (cudaMalloc may synchronise the device).
+ *
+ * All intermediates live in one fixed device array of ZK_STATIC_SCRATCH_BYTES
+ * inside the library, which every GPU that loads the library holds until the
+ * process exits. eta, psi (inputs) and v (output) are device pointers to
+ * FP32 [nz][nx] arrays owned by the caller. nx, nz: powers of two in
+ * [16, 256]; 1 <= M <= ZK_MAX_ORDER; eps in [0, 1]; taper 0/1. Sizes whose
+ * intermediates would not fit the array (e.g. 256 x 256 with M >= 7) are
+ * rejected with ZK_EINVAL before any GPU work; 256 x 256 fits up to M = 6.
+ * The work is queued on `stream` (cudaStream_t, NULL = legacy default) and
+ * the call returns without waiting; synchronise before reading v.
+ * The first call on each device looks up the array's device address, which
+ * may load the library's device code; make that first call before any stream
+ * capture. Every call on a device shares the array and overwrites what it
+ * needs, so calls whose GPU work overlaps (other streams or host threads on
+ * the same device) race and must be serialised by the caller. */
+#define ZK_STATIC_SCRATCH_BYTES (16u * 1024u * 1024u)
+zk_status zk_dno_static(const float *eta, const float *psi, float *v, int nx, int nz,
+                        double Lx, double Lz, double h, double g, int M, double eps, int taper,
+                        void *stream);
+
 /* Static text for a status code. */
 const char *zk_strerror(zk_status s);
 

@@ -14,7 +14,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libzk.so")
-SOURCES = [os.path.join(HERE, "csrc", "zk_api.cu")]
+SOURCES = [os.path.join(HERE, "csrc", "zk_api.cu"), os.path.join(HERE, "csrc", "zk_static.cu")]
 DEPS = SOURCES + [os.path.join(HERE, "csrc", f) for f in ("zk_fft.cuh", "zk_kernels.cuh")] + \
     [os.path.join(ROOT, "include", "zk.h")]
 

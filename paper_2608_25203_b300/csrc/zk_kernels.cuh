@@ -461,7 +461,7 @@ col_kernel(const ColArgs<T> a, const cx<T>* __restrict__ tw) {
     }
 }
 
-__global__ void energy_finalize_kernel(const double* __restrict__ partial, int n, double* __restrict__ out) {
+static __global__ void energy_finalize_kernel(const double* __restrict__ partial, int n, double* __restrict__ out) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         double s0 = 0, s1 = 0, s2 = 0;
         for (int i = 0; i < n; ++i) { s0 += partial[3 * i]; s1 += partial[3 * i + 1]; s2 += partial[3 * i + 2]; }

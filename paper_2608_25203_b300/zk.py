@@ -25,7 +25,7 @@ ZK_RK4, ZK_IFAB2 = 0, 1
 EXPORTS = [
     "zk_create", "zk_destroy", "zk_set_options", "zk_get_options", "zk_set_state", "zk_get_state",
     "zk_rhs", "zk_dno", "zk_step", "zk_energy", "zk_sync", "zk_device_bytes",
-    "zk_launches_per_step", "zk_profile_step", "zk_strerror", "zk_version",
+    "zk_launches_per_step", "zk_profile_step", "zk_dno_static", "zk_strerror", "zk_version",
 ]
 
 KERNEL_CLASSES = {0: "col_state", 1: "row_round", 2: "col_phi", 3: "row_final", 4: "col_final"}
@@ -70,6 +70,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "zk_device_bytes": ([vp, ctypes.POINTER(ctypes.c_size_t)], i),
         "zk_launches_per_step": ([vp, ctypes.POINTER(i)], i),
         "zk_profile_step": ([vp, d, i, pd, ctypes.POINTER(i), pd, i, ctypes.POINTER(i)], i),
+        "zk_dno_static": ([vp, vp, vp, i, i, d, d, d, d, i, d, i, vp], i),
         "zk_strerror": ([i], ctypes.c_char_p),
         "zk_version": ([], ctypes.c_char_p),
     }
@@ -189,6 +190,22 @@ def zk_profile_step(ctx, dt, nsteps=1, cap=256):
                                                      ctypes.byref(n)))
     k = n.value
     return list(ms[:k]), [KERNEL_CLASSES[x] for x in kind[:k]], list(by[:k])
+
+
+def zk_dno_static(eta, psi, v, Lx, Lz, h, g=9.81, M=5, eps=1.0, taper=1, stream=None):
+    """G(eta) psi into v with no device allocation (scratch is a fixed array in the library).
+
+    eta, psi, v: contiguous float32 CUDA tensors [nz][nx]. Queued on `stream`
+    (a cudaStream_t handle, None = legacy default); returns without waiting.
+    """
+    nz, nx = eta.shape
+    for t in (eta, psi, v):
+        pt, dev = _ptr(t, ZK_F32)
+        if not dev:
+            raise ValueError("zk_dno_static takes device tensors")
+    _check("zk_dno_static", load().zk_dno_static(eta.data_ptr(), psi.data_ptr(), v.data_ptr(), nx, nz,
+                                                 float(Lx), float(Lz), float(h), float(g), int(M), float(eps),
+                                                 int(taper), stream))
 
 
 def zk_version():
