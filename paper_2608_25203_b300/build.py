@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libzk.so")
 SOURCES = [os.path.join(HERE, "csrc", "zk_api.cu"), os.path.join(HERE, "csrc", "zk_static.cu")]
-DEPS = SOURCES + [os.path.join(HERE, "csrc", f) for f in ("zk_fft.cuh", "zk_kernels.cuh")] + \
+DEPS = SOURCES + [os.path.join(HERE, "csrc", f) for f in ("zk_fft.cuh", "zk_kernels.cuh", "zk_fft2.cuh", "zk_kernels2.cuh")] + \
     [os.path.join(ROOT, "include", "zk.h")]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -36,20 +36,34 @@ def up_to_date() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False, extra=None) -> str:
+    """Compile each translation unit in parallel, then link libzk.so."""
     if not force and up_to_date():
         return LIB
-    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
-           "-I", os.path.join(ROOT, "include"), "-o", LIB + ".tmp", *SOURCES]
+    flags = [*ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
     if verbose:
-        cmd.insert(1, "-Xptxas=-v")
+        flags.append("-Xptxas=-v")
     if extra:
-        cmd[1:1] = list(extra)
-    r = subprocess.run(cmd, capture_output=True, text=True)
+        flags += list(extra)
+    objs, procs = [], []
+    for src in SOURCES:
+        obj = os.path.join(HERE, os.path.basename(src) + ".o")
+        objs.append(obj)
+        procs.append((src, subprocess.Popen([nvcc(), *flags, "-c", "-o", obj, src], stdout=subprocess.PIPE,
+                                            stderr=subprocess.STDOUT, text=True)))
+    failed = False
+    for src, p in procs:
+        out, _ = p.communicate()
+        if p.returncode != 0 or verbose:
+            sys.stderr.write(out)
+        failed |= p.returncode != 0
+    if failed:
+        raise RuntimeError("nvcc failed")
+    r = subprocess.run([nvcc(), *ARCH, "-shared", "-o", LIB + ".tmp", *objs], capture_output=True, text=True)
     if r.returncode != 0:
         sys.stderr.write(r.stdout + r.stderr)
-        raise RuntimeError("nvcc failed")
-    if verbose:
-        sys.stderr.write(r.stderr)
+        raise RuntimeError("nvcc link failed")
+    for o in objs:
+        os.remove(o)
     os.replace(LIB + ".tmp", LIB)
     return LIB
 

@@ -13,11 +13,13 @@
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <string>
+#include <algorithm>
 #include <unordered_map>
 #include <vector>
 
 #include "../../include/zk.h"
-#include "zk_kernels.cuh"
+#include "zk_kernels2.cuh"
 
 using namespace zk;
 
@@ -25,7 +27,32 @@ namespace {
 
 constexpr int kIoElem = 8;  // bytes per staging element (fits f32 and f64)
 
-template <int NPZ> constexpr int col_cb() { return Plan<NPZ>::TL >= 64 ? 4 : (128 / Plan<NPZ>::TL); }
+// columns per column-kernel block: 4 for wide line groups, else enough for 128 (FP32) / 64 (FP64) threads
+template <int NPZ, int ES> constexpr int col_cb() { return IPlan<NPZ>::TL >= 64 ? 4 : ((ES == 8 ? 128 : 64) / IPlan<NPZ>::TL); }
+
+// Blocks of a persistent kernel: resident blocks per SM x SMs (cached per kernel shape).
+std::mutex g_occ_mu;
+std::unordered_map<std::string, int> g_occ;
+int persistent_grid(const void* fn, int threads, size_t smem, int work) {
+    char key[96];
+    snprintf(key, sizeof(key), "%p/%d/%zu", fn, threads, smem);
+    int per = 0;
+    {
+        std::lock_guard<std::mutex> lk(g_occ_mu);
+        auto it = g_occ.find(key);
+        if (it != g_occ.end()) per = it->second;
+    }
+    if (per == 0) {
+        int dev = 0, sms = 0, nb = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, smem);
+        per = std::max(1, nb) * std::max(1, sms);
+        std::lock_guard<std::mutex> lk(g_occ_mu);
+        g_occ[key] = per;
+    }
+    return std::min(work, per);
+}
 
 std::mutex g_attr_mu;
 std::unordered_map<const void*, int> g_attr;
@@ -70,6 +97,7 @@ struct zk_ctx {
     bool gvalid = false;
     double gdt = 0.0;
     int launches_per_step = 0;
+    int fin_blocks = 0;      // blocks of the last final column kernel (energy partials)
     // per-launch profiling (zk_profile_step): events recorded before each launch
     std::vector<cudaEvent_t>* prof_ev = nullptr;
     std::vector<int> slot_kind;
@@ -115,14 +143,21 @@ void make_twiddles(int n, std::vector<cx<T>>& out) {
 // ---------------------------------------------------------------------------
 template <typename T, int NPX>
 cudaError_t launch_row_t(const RowArgs<T>& a, const cx<T>* tw, int npz, cudaStream_t s) {
-    constexpr int TL = Plan<NPX>::TL;
-    int nl = a.nlines;
-    if constexpr (TL < 32) { constexpr int per = 32 / TL; nl = (nl + per - 1) / per * per; }
-    const int threads = nl * TL;
+    constexpr int TL = IPlan<NPX>::TL;
+    // narrow groups: one line per group, rounded to whole warps; wide groups:
+    // at most 512 threads, lines taken in waves
+    int nl = a.nlines, groups;
+    if constexpr (TL < 32) { constexpr int per = 32 / TL; nl = (nl + per - 1) / per * per; groups = nl; }
+    else groups = std::min(nl, 512 / TL);
+    const int threads = groups * TL;
     const size_t smem = (size_t)nl * line_stride(NPX) * sizeof(cx<T>);
-    cudaError_t e = ensure_smem((const void*)row_round_kernel<T, NPX>, smem);
+    const void* fn = (const void*)row2_kernel<T, NPX>;
+    cudaError_t e = ensure_smem(fn, smem);
     if (e != cudaSuccess) return e;
-    row_round_kernel<T, NPX><<<npz, threads, smem, s>>>(a, tw);
+    RowArgs<T> b = a;
+    b.npz = npz;
+    const int grid = persistent_grid(fn, threads, smem, npz);
+    row2_kernel<T, NPX><<<grid, threads, smem, s>>>(b, tw);
     return cudaGetLastError();
 }
 
@@ -143,19 +178,19 @@ cudaError_t launch_row(int npx, const RowArgs<T>& a, const cx<T>* tw, int npz, c
 
 template <typename T, int NPZ>
 cudaError_t launch_col_t(const ColArgs<T>& a, const cx<T>* tw, cudaStream_t s, int* nblocks) {
-    constexpr int TL = Plan<NPZ>::TL;
-    constexpr int CB = col_cb<NPZ>();
+    constexpr int TL = IPlan<NPZ>::TL;
+    constexpr int CB = col_cb<NPZ, (int)sizeof(cx<T>)>();
     constexpr int NZ = 2 * NPZ / 3;
     constexpr int LS = line_stride(NPZ);
     const int threads = CB * TL < 32 ? 32 : CB * TL;
     const int groups = threads / TL;
-    const size_t per = (a.kind == COL_FINAL) ? (size_t)2 * LS : (size_t)(LS + NZ);
+    const size_t per = (a.kind == COL_FINAL) ? (size_t)col_stride(2 * LS) : (size_t)col_stride(LS + NZ);
     const size_t smem = (size_t)groups * per * sizeof(cx<T>);
     const int grid = (a.hx + CB - 1) / CB;
     if (nblocks) *nblocks = grid;
-    cudaError_t e = ensure_smem((const void*)col_kernel<T, NPZ, CB>, smem);
+    cudaError_t e = ensure_smem((const void*)col2_kernel<T, NPZ, CB>, smem);
     if (e != cudaSuccess) return e;
-    col_kernel<T, NPZ, CB><<<grid, threads, smem, s>>>(a, tw);
+    col2_kernel<T, NPZ, CB><<<grid, threads, smem, s>>>(a, tw);
     return cudaGetLastError();
 }
 
@@ -174,7 +209,8 @@ cudaError_t launch_col(int npz, const ColArgs<T>& a, const cx<T>* tw, cudaStream
     }
 }
 
-template <int N> int col_blocks_for(int hx) { return (hx + col_cb<N>() - 1) / col_cb<N>(); }
+template <int N> int col_blocks_for(int hx) { return (hx + col_cb<N, 16>() - 1) / col_cb<N, 16>(); }
+// upper bound of column-kernel blocks (the FP64 blocking has the most blocks)
 int col_grid(int npz, int hx) {
     switch (npz) {
     case 24: return col_blocks_for<24>(hx); case 48: return col_blocks_for<48>(hx);
@@ -420,7 +456,7 @@ struct Pipe {
                 }
                 note(c, s, ZK_K_COL_FINAL, b);
             }
-            if ((e = launch_col<T>(c->npz, fin, twz, s)) != cudaSuccess) return e;
+            if ((e = launch_col<T>(c->npz, fin, twz, s, &c->fin_blocks)) != cudaSuccess) return e;
             ++nl;
         }
         if (nlaunch) *nlaunch += nl;
@@ -457,7 +493,7 @@ struct Pipe {
         fin.partial = c->partial;
         cudaError_t e = rhs(c, C(c->y_eta), C(c->y_psi), fin, s, nullptr);
         if (e != cudaSuccess) return e;
-        energy_finalize_kernel<<<1, 32, 0, s>>>(c->partial, col_grid(c->npz, c->hx), c->esum);
+        energy_finalize_kernel<<<1, 32, 0, s>>>(c->partial, c->fin_blocks, c->esum);
         return cudaGetLastError();
     }
 
@@ -485,13 +521,30 @@ struct Pipe {
     }
 };
 
+// Stockham tables (length-n w_n^t) for the unpadded state transforms; per-stage
+// tables of the in-place plans for the padded right-hand-side transforms.
+template <typename T>
+void make_plan_twiddles(int n, std::vector<cx<T>>& out) {
+    const PlanDesc d = plan_desc_of(n);
+    const int ne = plan_table_size(d);
+    out.resize(ne);
+    for (int e = 0; e < ne; ++e) {
+        long long num;
+        int den;
+        plan_table_entry(d, e, &num, &den);
+        const double ang = -2.0 * M_PI * (double)num / (double)den;
+        out[e] = mk<T>((T)std::cos(ang), (T)std::sin(ang));
+    }
+}
+
 template <typename T>
 zk_status alloc_twiddles(zk_ctx* c) {
     int ns[4] = {c->nx, c->nz, c->npx, c->npz};
     void** dst[4] = {&c->tw_x, &c->tw_z, &c->tw_px, &c->tw_pz};
     for (int i = 0; i < 4; ++i) {
         std::vector<cx<T>> h;
-        make_twiddles<T>(ns[i], h);
+        if (i < 2) make_twiddles<T>(ns[i], h);
+        else make_plan_twiddles<T>(ns[i], h);
         void* p = nullptr;
         if (cudaMalloc(&p, h.size() * sizeof(cx<T>)) != cudaSuccess) return ZK_ENOMEM;
         c->allocs.push_back(p);

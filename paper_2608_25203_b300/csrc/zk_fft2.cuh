@@ -1,0 +1,259 @@
+// zk_fft2.cuh - in-place digit-reversing line FFTs for the right-hand-side kernels.
+//
+// Decimation in frequency (DIF) takes a line in natural order and leaves its
+// transform in mixed-radix digit-reversed order; decimation in time (DIT)
+// takes digit-reversed input and produces natural order. Every stage works in
+// place: a butterfly reads R elements and writes its R results to the same
+// slots, so a thread holds only R complex values and stages need one group
+// barrier each.
+//
+// The right-hand side uses this pairing so that no reordering pass exists:
+// spectra are always in natural order (where the Fourier multipliers of
+// Sec. 3.2 and the truncation of Sec. 6.1 are applied), and physical values
+// on the 3/2 grid are always in digit-reversed order. Pointwise products do
+// not depend on the order, and every kernel that touches physical positions
+// (the row kernels, the column-space fields, the series accumulator) uses the
+// same plan, so the permutation cancels between an inverse (DIF) and the
+// following forward (DIT) transform.
+//
+// Stage with block size B and radix R (SUB = B/R): butterfly b has block
+// b/SUB and offset n1 = b mod SUB; it touches elements blk*B + n1 + m*SUB.
+// DIF: DFT_R then multiply output m by w_B^{n1 m}; DIT: multiply input m by
+// w_B^{n1 m} then DFT_R; DIT runs the stages in reverse order.
+#pragma once
+
+#include "zk_fft.cuh"
+
+namespace zk {
+
+// Shared-memory slot of element blk*B + n1 + m*SUB (n1 < SUB) of a stage. The
+// pad-per-16 layout lets each butterfly compute one base slot and add
+// compile-time offsets in three cases: SUB a multiple of 16; SUB dividing 16
+// inside 16-aligned blocks; blocks of 16/B elements (last stages).
+template <int B, int SUB>
+__device__ __forceinline__ int stage_pbase(int blk, int n1) {
+    if constexpr (SUB % 16 == 0) return pidx(blk * B + n1);
+    else if constexpr (SUB < 16 && 16 % SUB == 0 && B % 16 == 0) return blk * (B + B / 16) + n1;
+    else if constexpr (B < 16 && 16 % B == 0 && SUB == 1) return blk * B + ((blk * B) >> 4);
+    else return 0;
+}
+template <int B, int SUB>
+__device__ __forceinline__ int stage_slot(int pb, int base, int m) {
+    if constexpr (SUB % 16 == 0) return pb + m * (SUB + SUB / 16);
+    else if constexpr (SUB < 16 && 16 % SUB == 0 && B % 16 == 0) return pb + m * SUB + ((m * SUB) >> 4);
+    else if constexpr (B < 16 && 16 % B == 0 && SUB == 1) return pb + m;
+    else return pidx(base + m * SUB);
+}
+
+// Twiddles: one table per plan holding, stage after stage, w_B^{n1 m} at
+// [(m-1) * SUB + n1] (m = 1..R-1, n1 < SUB), so a warp's loads for one m are
+// contiguous. OFF is the stage's offset in that table.
+template <int N, int B, int R, int TL, bool INV, typename T, int OFF>
+__device__ __forceinline__ void dif_stage(cx<T>* buf, const cx<T>* __restrict__ tws, int lt) {
+    constexpr int SUB = B / R, NB = N / R;
+    static_assert(NB % TL == 0, "line group width must divide N/R");
+    // when TL is a multiple of SUB every butterfly of this thread has the same
+    // n1 = lt mod SUB: its R-1 twiddles are loaded once, before the loop
+    constexpr bool FIXED = (SUB > 1) && (TL % SUB == 0);
+    cx<T> wf[R > 1 ? R - 1 : 1];
+    if constexpr (FIXED) {
+#pragma unroll
+        for (int m = 1; m < R; ++m) wf[m - 1] = __ldg(&tws[OFF + (m - 1) * SUB + lt % SUB]);
+    }
+#pragma unroll
+    for (int p = 0; p < NB / TL; ++p) {
+        const int b = lt + p * TL;
+        const int blk = b / SUB, n1 = b - blk * SUB;
+        const int base = blk * B + n1;
+        const int pb = stage_pbase<B, SUB>(blk, n1);
+        cx<T> v[R];
+#pragma unroll
+        for (int m = 0; m < R; ++m) v[m] = buf[stage_slot<B, SUB>(pb, base, m)];
+        SmallDFT<R, INV, T>::run(v);
+        if (SUB > 1) {
+#pragma unroll
+            for (int m = 1; m < R; ++m)
+                v[m] = cmulc<INV>(v[m], FIXED ? wf[m - 1] : __ldg(&tws[OFF + (m - 1) * SUB + n1]));
+        }
+#pragma unroll
+        for (int m = 0; m < R; ++m) buf[stage_slot<B, SUB>(pb, base, m)] = v[m];
+    }
+}
+
+template <int N, int B, int R, int TL, bool INV, typename T, int OFF>
+__device__ __forceinline__ void dit_stage(cx<T>* buf, const cx<T>* __restrict__ tws, int lt) {
+    constexpr int SUB = B / R, NB = N / R;
+    static_assert(NB % TL == 0, "line group width must divide N/R");
+    // when TL is a multiple of SUB every butterfly of this thread has the same
+    // n1 = lt mod SUB: its R-1 twiddles are loaded once, before the loop
+    constexpr bool FIXED = (SUB > 1) && (TL % SUB == 0);
+    cx<T> wf[R > 1 ? R - 1 : 1];
+    if constexpr (FIXED) {
+#pragma unroll
+        for (int m = 1; m < R; ++m) wf[m - 1] = __ldg(&tws[OFF + (m - 1) * SUB + lt % SUB]);
+    }
+#pragma unroll
+    for (int p = 0; p < NB / TL; ++p) {
+        const int b = lt + p * TL;
+        const int blk = b / SUB, n1 = b - blk * SUB;
+        const int base = blk * B + n1;
+        const int pb = stage_pbase<B, SUB>(blk, n1);
+        cx<T> v[R];
+#pragma unroll
+        for (int m = 0; m < R; ++m) v[m] = buf[stage_slot<B, SUB>(pb, base, m)];
+        if (SUB > 1) {
+#pragma unroll
+            for (int m = 1; m < R; ++m)
+                v[m] = cmulc<INV>(v[m], FIXED ? wf[m - 1] : __ldg(&tws[OFF + (m - 1) * SUB + n1]));
+        }
+        SmallDFT<R, INV, T>::run(v);
+#pragma unroll
+        for (int m = 0; m < R; ++m) buf[stage_slot<B, SUB>(pb, base, m)] = v[m];
+    }
+}
+
+// First DIF stage (block N, table offset 0) reading its inputs through ld(p).
+template <int N, int R, int TL, bool INV, typename T, class Load>
+__device__ __forceinline__ void dif_first(cx<T>* buf, const cx<T>* __restrict__ tws, int lt, Load ld) {
+    constexpr int SUB = N / R;
+    static_assert(SUB % TL == 0, "line group width must divide N/R");
+#pragma unroll 2
+    for (int p = 0; p < SUB / TL; ++p) {
+        const int n1 = lt + p * TL;
+        cx<T> v[R];
+#pragma unroll
+        for (int m = 0; m < R; ++m) v[m] = ld(n1 + m * SUB, m * SUB);
+        SmallDFT<R, INV, T>::run(v);
+#pragma unroll
+        for (int m = 1; m < R; ++m) v[m] = cmulc<INV>(v[m], __ldg(&tws[(m - 1) * SUB + n1]));
+        const int pb = stage_pbase<N, SUB>(0, n1);
+#pragma unroll
+        for (int m = 0; m < R; ++m) buf[stage_slot<N, SUB>(pb, n1, m)] = v[m];
+    }
+}
+
+// Last DIT stage (block N): hands natural-order results to st(k, value).
+template <int N, int R, int TL, bool INV, typename T, class Store>
+__device__ __forceinline__ void dit_last(const cx<T>* buf, const cx<T>* __restrict__ tws, int lt, Store st) {
+    constexpr int SUB = N / R;
+    static_assert(SUB % TL == 0, "line group width must divide N/R");
+#pragma unroll 2
+    for (int p = 0; p < SUB / TL; ++p) {
+        const int n1 = lt + p * TL;
+        cx<T> v[R];
+        const int pb = stage_pbase<N, SUB>(0, n1);
+#pragma unroll
+        for (int m = 0; m < R; ++m) v[m] = buf[stage_slot<N, SUB>(pb, n1, m)];
+#pragma unroll
+        for (int m = 1; m < R; ++m) v[m] = cmulc<INV>(v[m], __ldg(&tws[(m - 1) * SUB + n1]));
+        SmallDFT<R, INV, T>::run(v);
+#pragma unroll
+        for (int m = 0; m < R; ++m) st(n1 + m * SUB, v[m]);
+    }
+}
+
+template <int N, int B, int TL, bool INV, typename T, int OFF, int R, int... Rest>
+__device__ __forceinline__ void dif_run(cx<T>* buf, const cx<T>* __restrict__ tws, int lt, int bar) {
+    dif_stage<N, B, R, TL, INV, T, OFF>(buf, tws, lt);
+    group_sync<TL>(bar);
+    if constexpr (sizeof...(Rest) > 0)
+        dif_run<N, B / R, TL, INV, T, OFF + (R - 1) * (B / R), Rest...>(buf, tws, lt, bar);
+}
+
+template <int N, int B, int TL, bool INV, typename T, int OFF, int R, int... Rest>
+__device__ __forceinline__ void dit_run(cx<T>* buf, const cx<T>* __restrict__ tws, int lt, int bar) {
+    if constexpr (sizeof...(Rest) > 0)
+        dit_run<N, B / R, TL, INV, T, OFF + (R - 1) * (B / R), Rest...>(buf, tws, lt, bar);
+    dit_stage<N, B, R, TL, INV, T, OFF>(buf, tws, lt);
+    group_sync<TL>(bar);
+}
+
+// Plans for the 3/2-padded line lengths: line-group width TL and radices in
+// DIF order. The last DIF stage is radix 16 (or 8 for the smallest line):
+// its stride-16 groups land on distinct banks with the pad-per-16 layout,
+// and TL divides N/R for every radix.
+template <int N> struct IPlan;
+#define ZK_IPLAN(N_, TL_, R1_, ...)                                                                      \
+    template <> struct IPlan<N_> {                                                                       \
+        static constexpr int TL = TL_, R1 = R1_;                                                         \
+        static constexpr int RADICES[] = {R1_, __VA_ARGS__};                                             \
+        static constexpr int NSTAGE = sizeof(RADICES) / sizeof(int);                                     \
+        template <bool INV, typename T, class Load>                                                      \
+        static __device__ __forceinline__ void dif(cx<T>* b, const cx<T>* __restrict__ tws, int lt,      \
+                                                   int bar, Load ld) {                                   \
+            dif_first<N_, R1_, TL_, INV, T>(b, tws, lt, ld);                                             \
+            group_sync<TL_>(bar);                                                                        \
+            dif_run<N_, N_ / R1_, TL_, INV, T, (R1_ - 1) * (N_ / R1_), __VA_ARGS__>(b, tws, lt, bar);    \
+        }                                                                                                \
+        template <bool INV, typename T, class Store>                                                     \
+        static __device__ __forceinline__ void dit(cx<T>* b, const cx<T>* __restrict__ tws, int lt,      \
+                                                   int bar, Store st) {                                  \
+            dit_run<N_, N_ / R1_, TL_, INV, T, (R1_ - 1) * (N_ / R1_), __VA_ARGS__>(b, tws, lt, bar);    \
+            dit_last<N_, R1_, TL_, INV, T>(b, tws, lt, st);                                              \
+        }                                                                                                \
+    };
+ZK_IPLAN(24, 1, 3, 8)
+ZK_IPLAN(48, 1, 3, 16)
+ZK_IPLAN(96, 2, 6, 16)
+ZK_IPLAN(192, 4, 12, 16)
+ZK_IPLAN(384, 8, 6, 4, 16)
+#ifdef ZK_RADIX16_PLANS
+ZK_IPLAN(768, 16, 3, 16, 16)
+ZK_IPLAN(1536, 32, 6, 16, 16)
+ZK_IPLAN(3072, 64, 12, 16, 16)
+#else
+// radix-8 plans: every stage has N/R divisible by 128 (3072), 64 (1536) or
+// 32 (768), twice the line-group width of the radix-16 plans at the same
+// shared memory per line; one 2-way bank conflict remains in the third stage
+ZK_IPLAN(768, 32, 3, 4, 8, 8)
+ZK_IPLAN(1536, 64, 3, 8, 8, 8)
+ZK_IPLAN(3072, 128, 6, 8, 8, 8)
+#endif
+#undef ZK_IPLAN
+
+// Host/device description of a plan for building its twiddle table.
+struct PlanDesc {
+    int n, nstage, radix[4];
+};
+template <int N> __host__ __device__ constexpr PlanDesc plan_desc() {
+    PlanDesc d{N, IPlan<N>::NSTAGE, {1, 1, 1, 1}};
+    for (int i = 0; i < IPlan<N>::NSTAGE; ++i) d.radix[i] = IPlan<N>::RADICES[i];
+    return d;
+}
+inline PlanDesc plan_desc_of(int n) {
+    switch (n) {
+    case 24: return plan_desc<24>();
+    case 48: return plan_desc<48>();
+    case 96: return plan_desc<96>();
+    case 192: return plan_desc<192>();
+    case 384: return plan_desc<384>();
+    case 768: return plan_desc<768>();
+    case 1536: return plan_desc<1536>();
+    case 3072: return plan_desc<3072>();
+    default: return PlanDesc{0, 0, {1, 1, 1, 1}};
+    }
+}
+// Number of table entries, and entry e as (numerator, B) of the angle -2 pi num / B.
+inline int plan_table_size(const PlanDesc& d) {
+    int n = 0, B = d.n;
+    for (int s = 0; s < d.nstage; ++s) { n += (d.radix[s] - 1) * (B / d.radix[s]); B /= d.radix[s]; }
+    return n;
+}
+__host__ __device__ inline void plan_table_entry(const PlanDesc& d, int e, long long* num, int* den) {
+    int B = d.n;
+    for (int s = 0; s < d.nstage; ++s) {
+        const int R = d.radix[s], SUB = B / R, cnt = (R - 1) * SUB;
+        if (e < cnt) {
+            const int m = 1 + e / SUB, n1 = e % SUB;
+            *num = ((long long)n1 * m) % B;
+            *den = B;
+            return;
+        }
+        e -= cnt;
+        B /= R;
+    }
+    *num = 0;
+    *den = 1;
+}
+
+}  // namespace zk

@@ -68,6 +68,7 @@ struct RowArgs {
     T* acc;                  // [npz][npx] series accumulator
     cx<T>* out0;             // column-space output (Phi(r), or G_nl)
     cx<T>* out1;             // N_psi (final round)
+    int npz;                 // padded rows (persistent row kernels loop over them)
 };
 
 template <typename T, int NPX>

@@ -1,0 +1,373 @@
+// zk_kernels2.cuh - row and column kernels of the right-hand side on the in-place
+// digit-reversing FFTs of zk_fft2.cuh (same argument blocks as zk_kernels.cuh).
+//
+// Order conventions: column-space row zp and position p of a padded row are
+// digit-reversed physical indices (written by DIF inverses, read by DIT
+// forwards of the same plan); spectra (compact fields, kx of a row, kz of a
+// column after a DIT) are in natural order.
+#pragma once
+
+#include "zk_fft2.cuh"
+#include "zk_kernels.cuh"
+
+namespace zk {
+
+template <typename T> __device__ __forceinline__ T tanh_kh(T x);
+// tanh(x) rounds to 1 in FP32 for x > 9.01 (1 - tanh < 2^-25) and in FP64 for x > 18.7.
+template <> __device__ __forceinline__ float tanh_kh<float>(float x) { return x > 9.5f ? 1.0f : tanhf(x); }
+template <> __device__ __forceinline__ double tanh_kh<double>(double x) { return x > 20.0 ? 1.0 : tanh(x); }
+
+// ---------------------------------------------------------------------------
+// Row kernel: persistent over padded rows.
+// ---------------------------------------------------------------------------
+template <typename T, int NPX>
+__global__ void __launch_bounds__(512) row2_kernel(const RowArgs<T> a, const cx<T>* __restrict__ tw) {
+    using P = IPlan<NPX>;
+    constexpr int TL = P::TL;
+    constexpr int HX = NPX / 3;
+    constexpr int LS = line_stride(NPX);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<T>* lines = reinterpret_cast<cx<T>*>(smem_raw);
+    const int g = threadIdx.x / TL, lt = threadIdx.x % TL;
+    const int bar = 1 + (g & 7);
+    const int ngroups = blockDim.x / TL;
+    // wide groups (TL >= 32) take lines in waves; narrow groups share warps and
+    // each runs exactly one line (idle ones on zeros) so warp barriers match
+    const int nloop = TL < 32 ? ngroups : a.nlines;
+    const T kx0 = a.kx0;
+    constexpr int SUB1 = NPX / P::R1;
+
+    for (int zp = blockIdx.x; zp < a.npz; zp += gridDim.x) {
+        // Phase A: Hermitian packing of two real fields fused into the first DIF stage.
+        for (int l = g; l < nloop; l += ngroups) {
+            cx<T>* lb = lines + (size_t)l * LS;
+            const bool act = l < a.nlines;
+            const int fa = act ? a.fa[l] : -1, fb = act ? a.fb[l] : -1;
+            const bool da = act && ((a.dxa >> l) & 1u), db = act && ((a.dxb >> l) & 1u);
+            const cx<T>* pa = fa >= 0 ? a.colbase + (long long)fa * a.fstride + (long long)zp * HX : nullptr;
+            const cx<T>* pb = fb >= 0 ? a.colbase + (long long)fb * a.fstride + (long long)zp * HX : nullptr;
+            // ms = m * SUB1 of the first stage (a compile-time constant after unrolling):
+            // the zero band, and in most cases the direct / mirror choice, follow from it.
+            auto ld = [&](int m, int ms) -> cx<T> {
+                int mm;
+                bool mir;
+                if (ms + SUB1 <= HX) { mm = m; mir = false; }
+                else if (ms >= HX && ms + SUB1 <= NPX - HX + 1) return mk<T>(0, 0);
+                else if (ms > NPX - HX) { mm = NPX - m; mir = true; }
+                else if (m < HX) { mm = m; mir = false; }
+                else if (m > NPX - HX) { mm = NPX - m; mir = true; }
+                else return mk<T>(0, 0);
+                cx<T> A = pa ? __ldg(pa + mm) : mk<T>(0, 0);
+                cx<T> B = pb ? __ldg(pb + mm) : mk<T>(0, 0);
+                const T kx = kx0 * (T)mm;
+                if (da) A = mk<T>(-kx * A.y, kx * A.x);
+                if (db) B = mk<T>(-kx * B.y, kx * B.x);
+                if (mm == 0) { A.y = 0; B.y = 0; }
+                return mir ? mk<T>(A.x + B.y, B.x - A.y) : mk<T>(A.x - B.y, A.y + B.x);
+            };
+            P::template dif<true, T>(lb, tw, lt, bar, ld);
+        }
+        __syncthreads();
+
+        // Phase B: pointwise HOS terms (positions in digit-reversed order).
+        auto slot = [&](int s, int p) -> T {
+            const cx<T> v = lines[(s >> 1) * LS + pidx(p)];
+            return (s & 1) ? v.y : v.x;
+        };
+        T* accrow = a.acc + (long long)zp * NPX;
+        for (int p = threadIdx.x; p < NPX; p += blockDim.x) {
+            if (a.kind == 0) {
+                const int r = a.r;
+                const T eta = slot(a.s_eta, p);
+                T W = 0, Phi = 0, ep = 1;
+                for (int q = 1; q <= r; ++q) {
+                    const T eq = ep * eta / (T)q;
+                    const T F = slot(a.s_F0 + (r - q), p);
+                    W += ep * F;
+                    Phi -= eq * F;
+                    ep = eq;
+                }
+                if (r >= 2) {
+                    T coef = a.epsp[r - 1];
+                    if (r - 1 <= a.M - 3) {
+                        const T ex = slot(a.s_etax, p), ez = slot(a.s_etaz, p);
+                        coef += a.epsp[r + 1] * (ex * ex + ez * ez);
+                    }
+                    const T prev = (r == 2) ? (T)0 : accrow[p];
+                    accrow[p] = prev + coef * W;
+                }
+                lines[pidx(p)] = mk<T>(Phi, 0);
+            } else {
+                const int M = a.M;
+                const T eps = a.eps;
+                const T ex = slot(a.s_etax, p), ez = slot(a.s_etaz, p);
+                const T px = slot(a.s_psix, p), pz = slot(a.s_psiz, p);
+                const T g0 = slot(a.s_g0psi, p);
+                const T g2 = ex * ex + ez * ez;
+                const T d = ex * px + ez * pz;
+                const T q2 = px * px + pz * pz;
+                T Gnl = 0;
+                if (M >= 2) {
+                    const T eta = slot(a.s_eta, p);
+                    T W = 0, ep = 1;
+                    for (int q = 1; q <= M; ++q) {
+                        W += ep * slot(a.s_F0 + (M - q), p);
+                        ep = ep * eta / (T)q;
+                    }
+                    Gnl = a.epsp[M - 1] * W - eps * d;
+                    if (M >= 3) Gnl += accrow[p] + a.epsp[2] * g2 * g0;
+                }
+                const T den = (T)1 + a.epsp[2] * g2;
+                const T Wb = (g0 + Gnl + eps * d) / den;
+                const T Np = eps * ((T)-0.5 * q2 + (T)0.5 * den * Wb * Wb);
+                lines[pidx(p)] = mk<T>(Gnl, Np);
+            }
+        }
+        __syncthreads();
+
+        // Phase C: forward DIT of line 0; keep kx < nx/2.
+        cx<T>* buf = lines + (size_t)g * LS;
+        if (threadIdx.x < 32 || g == 0) {
+            cx<T>* o0 = a.out0 + (long long)zp * HX;
+            if (a.kind == 0) {
+                const bool w = (g == 0);
+                P::template dit<false, T>(buf, tw, lt, bar, [&](int k, cx<T> v) {
+                    if (w && k < HX) o0[k] = v;
+                });
+            } else {
+                P::template dit<false, T>(buf, tw, lt, bar, [&](int k, cx<T> v) { buf[pidx(k)] = v; });
+                group_sync<TL>(bar);
+                if (g == 0) {
+                    cx<T>* o1 = a.out1 + (long long)zp * HX;
+                    for (int k = lt; k < HX; k += TL) {
+                        const cx<T> X = lines[pidx(k)];
+                        const cx<T> Y = cconj(lines[pidx(k == 0 ? 0 : NPX - k)]);
+                        o0[k] = cscale(cadd(X, Y), (T)0.5);
+                        const cx<T> D = csub(X, Y);
+                        o1[k] = mk<T>((T)0.5 * D.y, (T)-0.5 * D.x);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Column kernel: CB columns per block, tiles loaded and stored cooperatively.
+// ---------------------------------------------------------------------------
+// Per-column shared-memory stride (complex elements): rounded so that
+// stride = 4 (mod 16), which puts the CB columns of 4 consecutive rows of a
+// cooperative tile access on distinct 8-byte banks.
+__host__ __device__ constexpr int col_stride(int need) { return (need + 15) / 16 * 16 + 4; }
+
+template <typename T, int NPZ, int CB>
+__device__ __forceinline__ void col2_store_tile(const cx<T>* sm, int per, cx<T>* dst, int c0, int hx) {
+    constexpr int N = NPZ * CB;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const int z = i / CB, cg = i - z * CB;
+        if (c0 + cg < hx) dst[(long long)z * hx + c0 + cg] = sm[(size_t)cg * per + pidx(z)];
+    }
+}
+
+template <typename T, int NPZ, int CB>
+__global__ void __launch_bounds__(CB * IPlan<NPZ>::TL < 32 ? 32 : CB * IPlan<NPZ>::TL)
+col2_kernel(const ColArgs<T> a, const cx<T>* __restrict__ tw) {
+    using P = IPlan<NPZ>;
+    constexpr int TL = P::TL;
+    constexpr int NZ = 2 * NPZ / 3;
+    constexpr int LS = line_stride(NPZ);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
+    const int g = threadIdx.x / TL, lt = threadIdx.x % TL;
+    const int bar = 1 + (g & 7);
+    const int c0 = blockIdx.x * CB;
+    const int c = c0 + g;
+    const bool valid = (g < CB) && (c < a.hx);
+    const int cc = valid ? c : c0;
+    const T kx = a.kx0 * (T)cc;
+
+    if (a.kind == COL_FROM_STATE || a.kind == COL_PHI) {
+        constexpr int PER = col_stride(LS + NZ);
+        cx<T>* line = sm + (size_t)g * PER;
+        cx<T>* S = line + LS;
+        const int nsrc = a.kind == COL_FROM_STATE ? 2 : 1;
+        for (int src = 0; src < nsrc; ++src) {
+            if (a.kind == COL_FROM_STATE) {
+                const cx<T>* st = src == 0 ? a.st_eta : a.st_psi;
+                for (int i = threadIdx.x; i < NZ * CB; i += blockDim.x) {
+                    const int z = i / CB, cg = i - z * CB;
+                    const int col = c0 + cg;
+                    sm[(size_t)cg * PER + LS + z] = col < a.hx ? st[(long long)z * a.hx + col] : mk<T>(0, 0);
+                }
+                __syncthreads();
+            } else {
+                for (int i = threadIdx.x; i < NPZ * CB; i += blockDim.x) {
+                    const int z = i / CB, cg = i - z * CB;
+                    const int col = c0 + cg;
+                    sm[(size_t)cg * PER + pidx(z)] = col < a.hx ? a.pin[(long long)z * a.hx + col] : mk<T>(0, 0);
+                }
+                __syncthreads();
+                // forward DIT: truncate to the kept modes, scale and taper into S
+                const T fs = a.fscale;
+                P::template dit<false, T>(line, tw, lt, bar, [&](int k, cx<T> v) {
+                    int mz;
+                    if (k < NZ / 2) mz = k;
+                    else if (k > NPZ - NZ / 2) mz = k - NPZ;
+                    else return;
+                    const T kz = a.kz0 * (T)mz;
+                    T s = fs;
+                    if (a.taper) {
+                        const T kk2 = (kx * kx + kz * kz) / (a.kc * a.kc);
+                        const T k4 = kk2 * kk2;
+                        s *= d_exp(-(k4 * k4));
+                    }
+                    S[mz >= 0 ? mz : mz + NZ] = cscale(v, s);
+                });
+                if (lt == 0) S[NZ / 2] = mk<T>(0, 0);
+                __syncthreads();
+            }
+            for (int o = 0; o < a.nout; ++o) {
+                if (a.out_src[o] != src) continue;
+                const int sym = a.out_sym[o], aa = a.out_a[o];
+                const T isc = a.iscale;
+                constexpr int SUB1 = NPZ / P::R1;
+                auto ld = [&](int ip, int ms) -> cx<T> {
+                    int mz;
+                    if (ms + SUB1 <= NZ / 2) mz = ip;
+                    else if (ms >= NZ / 2 && ms + SUB1 <= NPZ - NZ / 2 + 1) return mk<T>(0, 0);
+                    else if (ms > NPZ - NZ / 2) mz = ip - NPZ;
+                    else if (ip < NZ / 2) mz = ip;
+                    else if (ip > NPZ - NZ / 2) mz = ip - NPZ;
+                    else return mk<T>(0, 0);
+                    const cx<T> s = S[mz >= 0 ? mz : mz + NZ];
+                    const T kz = a.kz0 * (T)mz;
+                    if (sym == SYM_ID) return cscale(s, isc);
+                    if (sym == SYM_DZ) return cscale(mk<T>(-kz * s.y, kz * s.x), isc);
+                    const T k2 = kx * kx + kz * kz;
+                    T f = isc;
+                    const int e2 = aa >> 1;
+                    for (int i = 0; i < e2; ++i) f *= k2;          // |k|^(2 floor(a/2))
+                    if (aa & 1) {                                  // odd a: one more G0 = |k| tanh(|k| h)
+                        const T k = d_sqrt(k2);
+                        f *= k * tanh_kh(k * a.h);
+                    }
+                    return cscale(s, f);
+                };
+                P::template dif<true, T>(line, tw, lt, bar, ld);
+                __syncthreads();
+                col2_store_tile<T, NPZ, CB>(sm, PER, a.colbase + (long long)a.out_f[o] * a.fstride, c0, a.hx);
+                __syncthreads();
+            }
+        }
+        return;
+    }
+
+    // COL_FINAL: two products, forward DIT, linear parts, epilogue per natural mode
+    constexpr int PER = col_stride(2 * LS);
+    cx<T>* l0 = sm + (size_t)g * PER;
+    cx<T>* l1 = l0 + LS;
+    for (int i = threadIdx.x; i < NPZ * CB; i += blockDim.x) {
+        const int z = i / CB, cg = i - z * CB;
+        const int col = c0 + cg;
+        const bool in = col < a.hx;
+        sm[(size_t)cg * PER + pidx(z)] = in ? a.gin[(long long)z * a.hx + col] : mk<T>(0, 0);
+        sm[(size_t)cg * PER + LS + pidx(z)] = in ? a.nin[(long long)z * a.hx + col] : mk<T>(0, 0);
+    }
+    __syncthreads();
+    P::template dit<false, T>(l0, tw, lt, bar, [&](int k, cx<T> v) { l0[pidx(k)] = v; });
+    P::template dit<false, T>(l1, tw, lt, bar, [&](int k, cx<T> v) { l1[pidx(k)] = v; });
+    group_sync<TL>(bar);
+
+    double e_kin = 0.0, e_pot = 0.0, e_bad = 0.0;
+    if (valid) {
+        const T ax = a.filter && a.mode == FIN_RK4
+                         ? (T)0.125 * ((T)5 + (T)4 * d_cospi((T)cc / (T)a.hx) - d_cospi((T)2 * (T)cc / (T)a.hx))
+                         : (T)1;
+        for (int ic = lt; ic < NZ; ic += TL) {
+            const long long idx = (long long)ic * a.hx + cc;
+            if (ic == NZ / 2) {
+                if (a.mode == FIN_RHS) { a.ko_eta[idx] = mk<T>(0, 0); a.ko_psi[idx] = mk<T>(0, 0); }
+                continue;
+            }
+            const int mz = ic < NZ / 2 ? ic : ic - NZ;
+            const int ip = mz >= 0 ? mz : mz + NPZ;
+            const T kz = a.kz0 * (T)mz;
+            const T k = d_sqrt(kx * kx + kz * kz);
+            T s = a.fscale;
+            if (a.taper) {
+                const T kk = k / a.kc;
+                const T k2 = kk * kk, k4 = k2 * k2;
+                s *= d_exp(-(k4 * k4));
+            }
+            cx<T> Fe = cscale(l0[pidx(ip)], s);
+            const cx<T> Fp = cscale(l1[pidx(ip)], s);
+            const cx<T> se = a.s_eta[idx], sp = a.s_psi[idx];
+            const T G0 = k * tanh_kh(k * a.h);
+            cx<T> de = cadd(cscale(sp, G0), Fe);
+            if (cc == 0 && mz == 0) de = mk<T>(0, 0);   // d eta/dt has zero mean
+            const cx<T> dp = cadd(cscale(se, -a.g), Fp);
+            switch (a.mode) {
+            case FIN_RHS:
+                a.ko_eta[idx] = de; a.ko_psi[idx] = dp;
+                break;
+            case FIN_RK1: {
+                a.ka_eta[idx] = de; a.ka_psi[idx] = dp;
+                const T hd = (T)0.5 * a.dt;
+                a.ys_eta[idx] = cadd(a.y_eta[idx], cscale(de, hd));
+                a.ys_psi[idx] = cadd(a.y_psi[idx], cscale(dp, hd));
+            } break;
+            case FIN_RK2:
+            case FIN_RK3: {
+                a.ka_eta[idx] = cadd(a.ka_eta[idx], cscale(de, (T)2));
+                a.ka_psi[idx] = cadd(a.ka_psi[idx], cscale(dp, (T)2));
+                const T hd = a.mode == FIN_RK2 ? (T)0.5 * a.dt : a.dt;
+                a.ys_eta[idx] = cadd(a.y_eta[idx], cscale(de, hd));
+                a.ys_psi[idx] = cadd(a.y_psi[idx], cscale(dp, hd));
+            } break;
+            case FIN_RK4: {
+                const T w = a.dt / (T)6;
+                T A = ax;
+                if (a.filter) {
+                    const T rz = (T)(mz < 0 ? -mz : mz) / (T)(NZ / 2);
+                    A *= (T)0.125 * ((T)5 + (T)4 * d_cospi(rz) - d_cospi((T)2 * rz));
+                }
+                const cx<T> ye = cadd(a.y_eta[idx], cscale(cadd(a.ka_eta[idx], de), w));
+                const cx<T> yp = cadd(a.y_psi[idx], cscale(cadd(a.ka_psi[idx], dp), w));
+                a.y_eta[idx] = cscale(ye, A);
+                a.y_psi[idx] = cscale(yp, A);
+            } break;
+            case FIN_ENERGY: {
+                const double wgt = cc == 0 ? 1.0 : 2.0;
+                e_kin += wgt * ((double)sp.x * (double)de.x + (double)sp.y * (double)de.y);
+                e_pot += wgt * ((double)se.x * (double)se.x + (double)se.y * (double)se.y);
+                const bool fin = isfinite((double)se.x) && isfinite((double)se.y) &&
+                                 isfinite((double)sp.x) && isfinite((double)sp.y);
+                if (!fin) e_bad += 1.0;
+            } break;
+            default: break;
+            }
+        }
+    }
+    if (a.mode == FIN_ENERGY) {
+        __shared__ double red[3][16];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            e_kin += __shfl_down_sync(0xffffffffu, e_kin, o);
+            e_pot += __shfl_down_sync(0xffffffffu, e_pot, o);
+            e_bad += __shfl_down_sync(0xffffffffu, e_bad, o);
+        }
+        const int w = threadIdx.x >> 5;
+        if ((threadIdx.x & 31) == 0) { red[0][w] = e_kin; red[1][w] = e_pot; red[2][w] = e_bad; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s0 = 0, s1 = 0, s2 = 0;
+            for (int t = 0; t < (int)(blockDim.x >> 5); ++t) { s0 += red[0][t]; s1 += red[1][t]; s2 += red[2][t]; }
+            a.partial[3 * blockIdx.x + 0] = s0;
+            a.partial[3 * blockIdx.x + 1] = s1;
+            a.partial[3 * blockIdx.x + 2] = s2;
+        }
+    }
+}
+
+}  // namespace zk

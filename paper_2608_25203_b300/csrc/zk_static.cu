@@ -19,7 +19,7 @@
 #include <mutex>
 
 #include "../../include/zk.h"
-#include "zk_kernels.cuh"
+#include "zk_kernels2.cuh"
 
 using namespace zk;
 
@@ -59,6 +59,19 @@ __global__ void static_twiddle_kernel(cx<float>* tw, int n) {
         double s, c;
         sincospi(-2.0 * (double)t / (double)n, &s, &c);
         tw[t] = mk<float>((float)c, (float)s);
+    }
+}
+
+// Per-stage table of an in-place plan (entry e = w_B^{n1 m}), FP64 on the device.
+__global__ void static_plan_twiddle_kernel(cx<float>* tw, PlanDesc d, int ne) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < ne) {
+        long long num;
+        int den;
+        plan_table_entry(d, e, &num, &den);
+        double s, c;
+        sincospi(-2.0 * (double)num / (double)den, &s, &c);
+        tw[e] = mk<float>((float)c, (float)s);
     }
 }
 
@@ -107,13 +120,16 @@ cudaError_t smem_attr(const void* fn, size_t bytes) {
 
 template <int NPX>
 cudaError_t s_row(const RowArgs<float>& a, const cx<float>* tw, int npz, cudaStream_t s) {
-    constexpr int TL = Plan<NPX>::TL;
-    int nl = a.nlines;
-    if constexpr (TL < 32) { constexpr int per = 32 / TL; nl = (nl + per - 1) / per * per; }
+    constexpr int TL = IPlan<NPX>::TL;
+    int nl = a.nlines, groups;
+    if constexpr (TL < 32) { constexpr int per = 32 / TL; nl = (nl + per - 1) / per * per; groups = nl; }
+    else groups = std::min(nl, 512 / TL);
     const size_t smem = (size_t)nl * line_stride(NPX) * sizeof(cx<float>);
-    cudaError_t e = smem_attr((const void*)row_round_kernel<float, NPX>, smem);
+    cudaError_t e = smem_attr((const void*)row2_kernel<float, NPX>, smem);
     if (e != cudaSuccess) return e;
-    row_round_kernel<float, NPX><<<npz, nl * TL, smem, s>>>(a, tw);
+    RowArgs<float> b = a;
+    b.npz = npz;
+    row2_kernel<float, NPX><<<npz, groups * TL, smem, s>>>(b, tw);
     return cudaGetLastError();
 }
 cudaError_t s_row_any(int npx, const RowArgs<float>& a, const cx<float>* tw, int npz, cudaStream_t s) {
@@ -129,16 +145,16 @@ cudaError_t s_row_any(int npx, const RowArgs<float>& a, const cx<float>* tw, int
 
 template <int NPZ>
 cudaError_t s_col(const ColArgs<float>& a, const cx<float>* tw, cudaStream_t s) {
-    constexpr int TL = Plan<NPZ>::TL;
+    constexpr int TL = IPlan<NPZ>::TL;
     constexpr int CB = TL >= 64 ? 4 : (128 / TL);
     constexpr int NZ = 2 * NPZ / 3;
     constexpr int LS = line_stride(NPZ);
     const int threads = CB * TL < 32 ? 32 : CB * TL;
-    const size_t per = (a.kind == COL_FINAL) ? (size_t)2 * LS : (size_t)(LS + NZ);
+    const size_t per = (a.kind == COL_FINAL) ? (size_t)col_stride(2 * LS) : (size_t)col_stride(LS + NZ);
     const size_t smem = (size_t)(threads / TL) * per * sizeof(cx<float>);
-    cudaError_t e = smem_attr((const void*)col_kernel<float, NPZ, CB>, smem);
+    cudaError_t e = smem_attr((const void*)col2_kernel<float, NPZ, CB>, smem);
     if (e != cudaSuccess) return e;
-    col_kernel<float, NPZ, CB><<<(a.hx + CB - 1) / CB, threads, smem, s>>>(a, tw);
+    col2_kernel<float, NPZ, CB><<<(a.hx + CB - 1) / CB, threads, smem, s>>>(a, tw);
     return cudaGetLastError();
 }
 cudaError_t s_col_any(int npz, const ColArgs<float>& a, const cx<float>* tw, cudaStream_t s) {
@@ -232,7 +248,13 @@ cudaError_t dno_static(unsigned char* base, const Layout& L, const float* eta, c
     const int ns[4] = {nx, nz, npx, npz};
     cx<float>* tws[4] = {twx, twz, twpx, twpz};
     for (int i = 0; i < 4; ++i) {
-        static_twiddle_kernel<<<(ns[i] + 127) / 128, 128, 0, s>>>(tws[i], ns[i]);
+        if (i < 2) {
+            static_twiddle_kernel<<<(ns[i] + 127) / 128, 128, 0, s>>>(tws[i], ns[i]);
+        } else {
+            const PlanDesc d = plan_desc_of(ns[i]);
+            const int ne = plan_table_size(d);
+            static_plan_twiddle_kernel<<<(ne + 127) / 128, 128, 0, s>>>(tws[i], d, ne);
+        }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     // physical -> compact spectra
