@@ -97,6 +97,11 @@ zk_status zk_dno(zk_ctx *ctx, void *v, int dtype, int on_device);
 /* Advance n steps of size dt with the selected integrator (each followed by
  * the state filter when enabled). Asynchronous on the context's stream; the
  * launch sequence of one step is captured once in a CUDA graph and replayed.
+ * ZK_RK4 evaluates the right-hand side four times per step. ZK_IFAB2 (Sec. 3.4)
+ * evaluates it once: the linear part is rotated exactly per mode (Eq. 14) and
+ * the nonlinear forcing enters through Eqs. 15-16 with F* = 3/2 F_n - 1/2 F_{n-1};
+ * the first step after zk_set_state, after an option change, or with a dt
+ * different from the previous step's uses F* = F_n (IF-Euler bootstrap).
  * ZK_ESTATE before zk_set_state. */
 zk_status zk_step(zk_ctx *ctx, double dt, int n);
 

@@ -81,6 +81,9 @@ struct zk_ctx {
     void *tw_x = nullptr, *tw_z = nullptr, *tw_px = nullptr, *tw_pz = nullptr;
     void *y_eta = nullptr, *y_psi = nullptr, *ys_eta = nullptr, *ys_psi = nullptr;
     void *ka_eta = nullptr, *ka_psi = nullptr, *ko_eta = nullptr, *ko_psi = nullptr;
+    void *h_eta = nullptr, *h_psi = nullptr;   // IF-AB2 forcing history
+    bool ab_valid = false;                     // history holds F_{n-1} taken at ab_dt
+    double ab_dt = 0.0;
     void *col = nullptr;
     int nfields = 0;
     long long fstride = 0;
@@ -93,7 +96,8 @@ struct zk_ctx {
     std::vector<void*> allocs;
     // graph of one step
     cudaStream_t cap = nullptr;
-    cudaGraphExec_t gexec = nullptr;
+    cudaGraphExec_t gexec = nullptr;      // RK4 step, or IF-AB2 step with history
+    cudaGraphExec_t gexec_boot = nullptr; // IF-AB2 bootstrap step (IF-Euler)
     bool gvalid = false;
     double gdt = 0.0;
     int launches_per_step = 0;
@@ -145,10 +149,10 @@ template <typename T, int NPX>
 cudaError_t launch_row_t(const RowArgs<T>& a, const cx<T>* tw, int npz, cudaStream_t s) {
     constexpr int TL = IPlan<NPX>::TL;
     // narrow groups: one line per group, rounded to whole warps; wide groups:
-    // at most 512 threads, lines taken in waves
+    // at most 1024 threads, lines beyond that taken in waves
     int nl = a.nlines, groups;
     if constexpr (TL < 32) { constexpr int per = 32 / TL; nl = (nl + per - 1) / per * per; groups = nl; }
-    else groups = std::min(nl, 512 / TL);
+    else groups = std::min(nl, 1024 / TL);
     const int threads = groups * TL;
     const size_t smem = (size_t)nl * line_stride(NPX) * sizeof(cx<T>);
     const void* fn = (const void*)row2_kernel<T, NPX>;
@@ -479,6 +483,16 @@ struct Pipe {
         return cudaSuccess;
     }
 
+    static cudaError_t ifab2_step(zk_ctx* c, double dt, bool first, cudaStream_t s, int* nlaunch) {
+        ColArgs<T> fin = col_base(c);
+        fin.mode = FIN_IFAB2;
+        fin.dt = (T)dt;
+        fin.ab_first = first ? 1 : 0;
+        fin.y_eta = C(c->y_eta); fin.y_psi = C(c->y_psi);
+        fin.h_eta = C(c->h_eta); fin.h_psi = C(c->h_psi);
+        return rhs(c, C(c->y_eta), C(c->y_psi), fin, s, nlaunch);
+    }
+
     static cudaError_t rhs_out(zk_ctx* c, cudaStream_t s) {
         ColArgs<T> fin = col_base(c);
         fin.mode = FIN_RHS;
@@ -565,17 +579,35 @@ zk_status dalloc(zk_ctx* c, void** p, size_t bytes) {
 
 void drop_graph(zk_ctx* c) {
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->gexec_boot) cudaGraphExecDestroy(c->gexec_boot);
     c->gexec = nullptr;
+    c->gexec_boot = nullptr;
     c->gvalid = false;
 }
 
-template <typename T>
-cudaError_t enqueue_step(zk_ctx* c, double dt, cudaStream_t s, int* nl) {
-    return Pipe<T>::rk4_step(c, dt, s, nl);
+// variant: 0 = RK4 step, 1 = IF-AB2 bootstrap step, 2 = IF-AB2 step with history
+cudaError_t enqueue_step_any(zk_ctx* c, double dt, cudaStream_t s, int* nl, int variant) {
+    if (variant == 0)
+        return c->prec == ZK_F32 ? Pipe<float>::rk4_step(c, dt, s, nl) : Pipe<double>::rk4_step(c, dt, s, nl);
+    const bool first = variant == 1;
+    return c->prec == ZK_F32 ? Pipe<float>::ifab2_step(c, dt, first, s, nl)
+                             : Pipe<double>::ifab2_step(c, dt, first, s, nl);
 }
 
-cudaError_t enqueue_step_any(zk_ctx* c, double dt, cudaStream_t s, int* nl) {
-    return c->prec == ZK_F32 ? enqueue_step<float>(c, dt, s, nl) : enqueue_step<double>(c, dt, s, nl);
+zk_status capture(zk_ctx* c, double dt, int variant, cudaGraphExec_t* out, int* nl) {
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeRelaxed) != cudaSuccess) return ZK_ECUDA;
+    cudaError_t e = enqueue_step_any(c, dt, c->cap, nl, variant);
+    cudaError_t e2 = cudaStreamEndCapture(c->cap, &graph);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return ZK_ECUDA;
+    }
+    e = cudaGraphInstantiate(out, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) { *out = nullptr; return ZK_ECUDA; }
+    return ZK_OK;
 }
 
 zk_status build_graph(zk_ctx* c, double dt) {
@@ -583,19 +615,17 @@ zk_status build_graph(zk_ctx* c, double dt) {
     if (!c->cap) {
         if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) return ZK_ECUDA;
     }
-    cudaGraph_t graph = nullptr;
-    if (cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeRelaxed) != cudaSuccess) return ZK_ECUDA;
     int nl = 0;
-    cudaError_t e = enqueue_step_any(c, dt, c->cap, &nl);
-    cudaError_t e2 = cudaStreamEndCapture(c->cap, &graph);
-    if (e != cudaSuccess || e2 != cudaSuccess) {
-        if (graph) cudaGraphDestroy(graph);
-        cudaGetLastError();
-        return ZK_ECUDA;
+    zk_status st;
+    if (c->opt.integrator == ZK_IFAB2) {
+        st = capture(c, dt, 1, &c->gexec_boot, &nl);
+        if (st != ZK_OK) return st;
+        nl = 0;
+        st = capture(c, dt, 2, &c->gexec, &nl);
+    } else {
+        st = capture(c, dt, 0, &c->gexec, &nl);
     }
-    e = cudaGraphInstantiate(&c->gexec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (e != cudaSuccess) { c->gexec = nullptr; return ZK_ECUDA; }
+    if (st != ZK_OK) { drop_graph(c); return st; }
     c->gvalid = true;
     c->gdt = dt;
     c->launches_per_step = nl;
@@ -665,8 +695,9 @@ zk_status zk_create(zk_ctx** out, int nx, int nz, double Lx, double Lz, double h
     const size_t rsz = precision == ZK_F32 ? 4 : 8;
     zk_status st = precision == ZK_F32 ? alloc_twiddles<float>(c) : alloc_twiddles<double>(c);
     const size_t compact = (size_t)nz * c->hx * c->csz;
-    void** comp[8] = {&c->y_eta, &c->y_psi, &c->ys_eta, &c->ys_psi, &c->ka_eta, &c->ka_psi, &c->ko_eta, &c->ko_psi};
-    for (int i = 0; i < 8 && st == ZK_OK; ++i) st = dalloc(c, comp[i], compact);
+    void** comp[10] = {&c->y_eta, &c->y_psi, &c->ys_eta, &c->ys_psi, &c->ka_eta, &c->ka_psi,
+                       &c->ko_eta, &c->ko_psi, &c->h_eta, &c->h_psi};
+    for (int i = 0; i < 10 && st == ZK_OK; ++i) st = dalloc(c, comp[i], compact);
     const Fields F{M};
     c->nfields = F.count();
     c->fstride = (long long)c->npz * c->hx;
@@ -686,7 +717,8 @@ zk_status zk_set_options(zk_ctx* c, const zk_options* o) {
     if (!(o->eps >= 0.0 && o->eps <= 1.0)) return ZK_EINVAL;
     if (o->integrator != ZK_RK4 && o->integrator != ZK_IFAB2) return ZK_EINVAL;
     if ((o->taper != 0 && o->taper != 1) || (o->filter != 0 && o->filter != 1)) return ZK_EINVAL;
-    if (o->integrator == ZK_IFAB2) return ZK_EUNSUPPORTED;
+    if (o->integrator != c->opt.integrator || o->eps != c->opt.eps || o->taper != c->opt.taper)
+        c->ab_valid = false;   // the forcing history belongs to the old right-hand side
     c->opt = *o;
     drop_graph(c);
     return ZK_OK;
@@ -707,6 +739,7 @@ zk_status zk_set_state(zk_ctx* c, const void* eta, const void* psi, int dtype, i
                                       : Pipe<double>::set_state(c, de, dp, dtype, user_stream(c));
     if (e != cudaSuccess) return ZK_ECUDA;
     c->has_state = true;
+    c->ab_valid = false;
     return ZK_OK;
 }
 
@@ -762,8 +795,16 @@ zk_status zk_step(zk_ctx* c, double dt, int n) {
         if (st != ZK_OK) return st;
     }
     cudaStream_t s = user_stream(c);
-    for (int i = 0; i < n; ++i)
-        if (cudaGraphLaunch(c->gexec, s) != cudaSuccess) return ZK_ECUDA;
+    for (int i = 0; i < n; ++i) {
+        cudaGraphExec_t g = c->gexec;
+        if (c->opt.integrator == ZK_IFAB2 && !(c->ab_valid && c->ab_dt == dt)) {
+            // first step, or a step whose dt differs from the history's: IF-Euler (Sec. 3.4)
+            g = c->gexec_boot;
+            c->ab_valid = true;
+            c->ab_dt = dt;
+        }
+        if (cudaGraphLaunch(g, s) != cudaSuccess) return ZK_ECUDA;
+    }
     return ZK_OK;
 }
 
@@ -810,7 +851,13 @@ zk_status zk_profile_step(zk_ctx* c, double dt, int nsteps, double* ms, int* kin
         c->slot_kind.clear();
         c->slot_bytes.clear();
         int nl = 0;
-        cudaError_t e = enqueue_step_any(c, dt, s, &nl);
+        int variant = 0;
+        if (c->opt.integrator == ZK_IFAB2) {
+            variant = (c->ab_valid && c->ab_dt == dt) ? 2 : 1;
+            c->ab_valid = true;
+            c->ab_dt = dt;
+        }
+        cudaError_t e = enqueue_step_any(c, dt, s, &nl, variant);
         cudaEvent_t last;
         cudaEventCreate(&last);
         cudaEventRecord(last, s);
@@ -854,7 +901,7 @@ zk_status zk_device_bytes(const zk_ctx* c, size_t* b) {
 
 zk_status zk_launches_per_step(const zk_ctx* c, int* n) {
     if (!c || !n) return ZK_EINVAL;
-    *n = 4 * (2 * c->M + 1);
+    *n = (c->opt.integrator == ZK_IFAB2 ? 1 : 4) * (2 * c->M + 1);
     return ZK_OK;
 }
 

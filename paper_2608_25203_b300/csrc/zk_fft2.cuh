@@ -168,6 +168,54 @@ __device__ __forceinline__ void dit_run(cx<T>* buf, const cx<T>* __restrict__ tw
     group_sync<TL>(bar);
 }
 
+// ---- whole-block variants: every thread of the block works on one line ----
+// (nt = blockDim.x threads, __syncthreads between stages). Used where one
+// line must be transformed while the rest of the block would otherwise idle.
+template <int N, int B, int R, bool INV, typename T, int OFF>
+__device__ __forceinline__ void dit_stage_blk(cx<T>* buf, const cx<T>* __restrict__ tws, int tid, int nt) {
+    constexpr int SUB = B / R, NB = N / R;
+    for (int b = tid; b < NB; b += nt) {
+        const int blk = b / SUB, n1 = b - blk * SUB;
+        const int base = blk * B + n1;
+        const int pb = stage_pbase<B, SUB>(blk, n1);
+        cx<T> v[R];
+#pragma unroll
+        for (int m = 0; m < R; ++m) v[m] = buf[stage_slot<B, SUB>(pb, base, m)];
+        if (SUB > 1) {
+#pragma unroll
+            for (int m = 1; m < R; ++m) v[m] = cmulc<INV>(v[m], __ldg(&tws[OFF + (m - 1) * SUB + n1]));
+        }
+        SmallDFT<R, INV, T>::run(v);
+#pragma unroll
+        for (int m = 0; m < R; ++m) buf[stage_slot<B, SUB>(pb, base, m)] = v[m];
+    }
+}
+
+template <int N, int B, bool INV, typename T, int OFF, int R, int... Rest>
+__device__ __forceinline__ void dit_run_blk(cx<T>* buf, const cx<T>* __restrict__ tws, int tid, int nt) {
+    if constexpr (sizeof...(Rest) > 0)
+        dit_run_blk<N, B / R, INV, T, OFF + (R - 1) * (B / R), Rest...>(buf, tws, tid, nt);
+    dit_stage_blk<N, B, R, INV, T, OFF>(buf, tws, tid, nt);
+    __syncthreads();
+}
+
+template <int N, int R, bool INV, typename T, class Store>
+__device__ __forceinline__ void dit_last_blk(const cx<T>* buf, const cx<T>* __restrict__ tws, int tid, int nt,
+                                             Store st) {
+    constexpr int SUB = N / R;
+    for (int n1 = tid; n1 < SUB; n1 += nt) {
+        cx<T> v[R];
+        const int pb = stage_pbase<N, SUB>(0, n1);
+#pragma unroll
+        for (int m = 0; m < R; ++m) v[m] = buf[stage_slot<N, SUB>(pb, n1, m)];
+#pragma unroll
+        for (int m = 1; m < R; ++m) v[m] = cmulc<INV>(v[m], __ldg(&tws[(m - 1) * SUB + n1]));
+        SmallDFT<R, INV, T>::run(v);
+#pragma unroll
+        for (int m = 0; m < R; ++m) st(n1 + m * SUB, v[m]);
+    }
+}
+
 // Plans for the 3/2-padded line lengths: line-group width TL and radices in
 // DIF order. The last DIF stage is radix 16 (or 8 for the smallest line):
 // its stride-16 groups land on distinct banks with the pad-per-16 layout,
@@ -190,6 +238,12 @@ template <int N> struct IPlan;
                                                    int bar, Store st) {                                  \
             dit_run<N_, N_ / R1_, TL_, INV, T, (R1_ - 1) * (N_ / R1_), __VA_ARGS__>(b, tws, lt, bar);    \
             dit_last<N_, R1_, TL_, INV, T>(b, tws, lt, st);                                              \
+        }                                                                                                \
+        template <bool INV, typename T, class Store>                                                     \
+        static __device__ __forceinline__ void dit_blk(cx<T>* b, const cx<T>* __restrict__ tws, int tid, \
+                                                       int nt, Store st) {                               \
+            dit_run_blk<N_, N_ / R1_, INV, T, (R1_ - 1) * (N_ / R1_), __VA_ARGS__>(b, tws, tid, nt);     \
+            dit_last_blk<N_, R1_, INV, T>(b, tws, tid, nt, st);                                          \
         }                                                                                                \
     };
 ZK_IPLAN(24, 1, 3, 8)

@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(512) row_round_kernel(const RowArgs<T> a, cons
 // ---------------------------------------------------------------------------
 enum ColKind { COL_FROM_STATE = 0, COL_PHI = 1, COL_FINAL = 2 };
 enum ColSym { SYM_ID = 0, SYM_DZ = 1, SYM_ZA = 2 };
-enum FinalMode { FIN_RHS = 0, FIN_RK1 = 1, FIN_RK2 = 2, FIN_RK3 = 3, FIN_RK4 = 4, FIN_ENERGY = 5 };
+enum FinalMode { FIN_RHS = 0, FIN_RK1 = 1, FIN_RK2 = 2, FIN_RK3 = 3, FIN_RK4 = 4, FIN_ENERGY = 5, FIN_IFAB2 = 6 };
 
 template <typename T>
 struct ColArgs {
@@ -228,6 +228,8 @@ struct ColArgs {
     int filter;
     int nx_grid;
     double* partial;          // energy: [gridDim.x][3]
+    cx<T>* h_eta; cx<T>* h_psi;     // IF-AB2: nonlinear forcing of the previous step
+    int ab_first;                   // IF-AB2: 1 = bootstrap with IF-Euler (F* = F_n)
 };
 
 template <typename T>

@@ -17,11 +17,15 @@ template <typename T> __device__ __forceinline__ T tanh_kh(T x);
 template <> __device__ __forceinline__ float tanh_kh<float>(float x) { return x > 9.5f ? 1.0f : tanhf(x); }
 template <> __device__ __forceinline__ double tanh_kh<double>(double x) { return x > 20.0 ? 1.0 : tanh(x); }
 
+template <typename T> __device__ __forceinline__ void d_sincos(T x, T* s, T* c);
+template <> __device__ __forceinline__ void d_sincos<float>(float x, float* s, float* c) { sincosf(x, s, c); }
+template <> __device__ __forceinline__ void d_sincos<double>(double x, double* s, double* c) { sincos(x, s, c); }
+
 // ---------------------------------------------------------------------------
 // Row kernel: persistent over padded rows.
 // ---------------------------------------------------------------------------
 template <typename T, int NPX>
-__global__ void __launch_bounds__(512) row2_kernel(const RowArgs<T> a, const cx<T>* __restrict__ tw) {
+__global__ void __launch_bounds__(1024) row2_kernel(const RowArgs<T> a, const cx<T>* __restrict__ tw) {
     using P = IPlan<NPX>;
     constexpr int TL = P::TL;
     constexpr int HX = NPX / 3;
@@ -125,27 +129,24 @@ __global__ void __launch_bounds__(512) row2_kernel(const RowArgs<T> a, const cx<
         }
         __syncthreads();
 
-        // Phase C: forward DIT of line 0; keep kx < nx/2.
-        cx<T>* buf = lines + (size_t)g * LS;
-        if (threadIdx.x < 32 || g == 0) {
+        // Phase C: forward DIT of line 0 by the whole block; keep kx < nx/2.
+        {
             cx<T>* o0 = a.out0 + (long long)zp * HX;
             if (a.kind == 0) {
-                const bool w = (g == 0);
-                P::template dit<false, T>(buf, tw, lt, bar, [&](int k, cx<T> v) {
-                    if (w && k < HX) o0[k] = v;
+                P::template dit_blk<false, T>(lines, tw, threadIdx.x, blockDim.x, [&](int k, cx<T> v) {
+                    if (k < HX) o0[k] = v;
                 });
             } else {
-                P::template dit<false, T>(buf, tw, lt, bar, [&](int k, cx<T> v) { buf[pidx(k)] = v; });
-                group_sync<TL>(bar);
-                if (g == 0) {
-                    cx<T>* o1 = a.out1 + (long long)zp * HX;
-                    for (int k = lt; k < HX; k += TL) {
-                        const cx<T> X = lines[pidx(k)];
-                        const cx<T> Y = cconj(lines[pidx(k == 0 ? 0 : NPX - k)]);
-                        o0[k] = cscale(cadd(X, Y), (T)0.5);
-                        const cx<T> D = csub(X, Y);
-                        o1[k] = mk<T>((T)0.5 * D.y, (T)-0.5 * D.x);
-                    }
+                P::template dit_blk<false, T>(lines, tw, threadIdx.x, blockDim.x,
+                                              [&](int k, cx<T> v) { lines[pidx(k)] = v; });
+                __syncthreads();
+                cx<T>* o1 = a.out1 + (long long)zp * HX;
+                for (int k = threadIdx.x; k < HX; k += blockDim.x) {
+                    const cx<T> X = lines[pidx(k)];
+                    const cx<T> Y = cconj(lines[pidx(k == 0 ? 0 : NPX - k)]);
+                    o0[k] = cscale(cadd(X, Y), (T)0.5);
+                    const cx<T> D = csub(X, Y);
+                    o1[k] = mk<T>((T)0.5 * D.y, (T)-0.5 * D.x);
                 }
             }
         }
@@ -277,76 +278,119 @@ col2_kernel(const ColArgs<T> a, const cx<T>* __restrict__ tw) {
     __syncthreads();
     P::template dit<false, T>(l0, tw, lt, bar, [&](int k, cx<T> v) { l0[pidx(k)] = v; });
     P::template dit<false, T>(l1, tw, lt, bar, [&](int k, cx<T> v) { l1[pidx(k)] = v; });
-    group_sync<TL>(bar);
+    __syncthreads();
 
+    // Epilogue over the CB-column tile: consecutive threads take adjacent
+    // columns of one kz row, so the state arrays move in 8*CB-byte segments.
     double e_kin = 0.0, e_pot = 0.0, e_bad = 0.0;
-    if (valid) {
-        const T ax = a.filter && a.mode == FIN_RK4
-                         ? (T)0.125 * ((T)5 + (T)4 * d_cospi((T)cc / (T)a.hx) - d_cospi((T)2 * (T)cc / (T)a.hx))
-                         : (T)1;
-        for (int ic = lt; ic < NZ; ic += TL) {
-            const long long idx = (long long)ic * a.hx + cc;
-            if (ic == NZ / 2) {
-                if (a.mode == FIN_RHS) { a.ko_eta[idx] = mk<T>(0, 0); a.ko_psi[idx] = mk<T>(0, 0); }
-                continue;
+    for (int i = threadIdx.x; i < NZ * CB; i += blockDim.x) {
+        const int ic = i / CB, cg = i - ic * CB;
+        const int col = c0 + cg;
+        if (col >= a.hx) continue;
+        const long long idx = (long long)ic * a.hx + col;
+        if (ic == NZ / 2) {
+            if (a.mode == FIN_RHS) { a.ko_eta[idx] = mk<T>(0, 0); a.ko_psi[idx] = mk<T>(0, 0); }
+            continue;
+        }
+        const int mz = ic < NZ / 2 ? ic : ic - NZ;
+        const int ip = mz >= 0 ? mz : mz + NPZ;
+        const T kxc = a.kx0 * (T)col;
+        const T kz = a.kz0 * (T)mz;
+        const T k = d_sqrt(kxc * kxc + kz * kz);
+        T s = a.fscale;
+        if (a.taper) {
+            const T kk = k / a.kc;
+            const T k2 = kk * kk, k4 = k2 * k2;
+            s *= d_exp(-(k4 * k4));
+        }
+        const cx<T>* lc = sm + (size_t)cg * PER;
+        cx<T> Fe = cscale(lc[pidx(ip)], s);
+        const cx<T> Fp = cscale(lc[LS + pidx(ip)], s);
+        const cx<T> se = a.s_eta[idx], sp = a.s_psi[idx];
+        const T G0 = k * tanh_kh(k * a.h);
+        if (col == 0 && mz == 0) Fe = mk<T>(0, 0);   // d eta/dt has zero mean
+        cx<T> de = cadd(cscale(sp, G0), Fe);
+        if (col == 0 && mz == 0) de = mk<T>(0, 0);
+        const cx<T> dp = cadd(cscale(se, -a.g), Fp);
+        switch (a.mode) {
+        case FIN_IFAB2: {
+            // Eqs. 15-16: exact linear rotation plus the Duhamel response to the
+            // AB2-extrapolated forcing F* (IF-Euler at the first step).
+            cx<T> Fse = Fe, Fsp = Fp;
+            if (!a.ab_first) {
+                Fse = csub(cscale(Fe, (T)1.5), cscale(a.h_eta[idx], (T)0.5));
+                Fsp = csub(cscale(Fp, (T)1.5), cscale(a.h_psi[idx], (T)0.5));
             }
-            const int mz = ic < NZ / 2 ? ic : ic - NZ;
-            const int ip = mz >= 0 ? mz : mz + NPZ;
-            const T kz = a.kz0 * (T)mz;
-            const T k = d_sqrt(kx * kx + kz * kz);
-            T s = a.fscale;
-            if (a.taper) {
-                const T kk = k / a.kc;
-                const T k2 = kk * kk, k4 = k2 * k2;
-                s *= d_exp(-(k4 * k4));
+            a.h_eta[idx] = Fe;
+            a.h_psi[idx] = Fp;
+            const T w = d_sqrt(a.g * G0);
+            T c, sw, G0sw, gsw, omc_g, omc_G0;
+            if (w > (T)0) {
+                T sh, ch;                              // half angle: one sincos gives both
+                d_sincos((T)0.5 * w * a.dt, &sh, &ch);
+                const T omc = (T)2 * sh * sh;          // 1 - cos(w dt) without cancellation
+                c = (T)1 - omc;
+                sw = (T)2 * sh * ch / w;               // sin(w dt) / w
+                G0sw = G0 * sw;                        // (G0 / w) sin(w dt)
+                gsw = a.g * sw;                        // (g / w) sin(w dt)
+                omc_g = omc / a.g;
+                omc_G0 = omc / G0;
+            } else {                                   // k = 0 limits stated under Eq. 16
+                c = 1; sw = a.dt; G0sw = 0; gsw = a.g * a.dt; omc_g = 0; omc_G0 = (T)0.5 * a.g * a.dt * a.dt;
             }
-            cx<T> Fe = cscale(l0[pidx(ip)], s);
-            const cx<T> Fp = cscale(l1[pidx(ip)], s);
-            const cx<T> se = a.s_eta[idx], sp = a.s_psi[idx];
-            const T G0 = k * tanh_kh(k * a.h);
-            cx<T> de = cadd(cscale(sp, G0), Fe);
-            if (cc == 0 && mz == 0) de = mk<T>(0, 0);   // d eta/dt has zero mean
-            const cx<T> dp = cadd(cscale(se, -a.g), Fp);
-            switch (a.mode) {
-            case FIN_RHS:
-                a.ko_eta[idx] = de; a.ko_psi[idx] = dp;
-                break;
-            case FIN_RK1: {
-                a.ka_eta[idx] = de; a.ka_psi[idx] = dp;
-                const T hd = (T)0.5 * a.dt;
-                a.ys_eta[idx] = cadd(a.y_eta[idx], cscale(de, hd));
-                a.ys_psi[idx] = cadd(a.y_psi[idx], cscale(dp, hd));
-            } break;
-            case FIN_RK2:
-            case FIN_RK3: {
-                a.ka_eta[idx] = cadd(a.ka_eta[idx], cscale(de, (T)2));
-                a.ka_psi[idx] = cadd(a.ka_psi[idx], cscale(dp, (T)2));
-                const T hd = a.mode == FIN_RK2 ? (T)0.5 * a.dt : a.dt;
-                a.ys_eta[idx] = cadd(a.y_eta[idx], cscale(de, hd));
-                a.ys_psi[idx] = cadd(a.y_psi[idx], cscale(dp, hd));
-            } break;
-            case FIN_RK4: {
-                const T w = a.dt / (T)6;
-                T A = ax;
-                if (a.filter) {
-                    const T rz = (T)(mz < 0 ? -mz : mz) / (T)(NZ / 2);
-                    A *= (T)0.125 * ((T)5 + (T)4 * d_cospi(rz) - d_cospi((T)2 * rz));
-                }
-                const cx<T> ye = cadd(a.y_eta[idx], cscale(cadd(a.ka_eta[idx], de), w));
-                const cx<T> yp = cadd(a.y_psi[idx], cscale(cadd(a.ka_psi[idx], dp), w));
-                a.y_eta[idx] = cscale(ye, A);
-                a.y_psi[idx] = cscale(yp, A);
-            } break;
-            case FIN_ENERGY: {
-                const double wgt = cc == 0 ? 1.0 : 2.0;
-                e_kin += wgt * ((double)sp.x * (double)de.x + (double)sp.y * (double)de.y);
-                e_pot += wgt * ((double)se.x * (double)se.x + (double)se.y * (double)se.y);
-                const bool fin = isfinite((double)se.x) && isfinite((double)se.y) &&
-                                 isfinite((double)sp.x) && isfinite((double)sp.y);
-                if (!fin) e_bad += 1.0;
-            } break;
-            default: break;
+            cx<T> e1 = cadd(cadd(cscale(se, c), cscale(sp, G0sw)), cadd(cscale(Fse, sw), cscale(Fsp, omc_g)));
+            cx<T> p1 = cadd(csub(cscale(sp, c), cscale(se, gsw)), csub(cscale(Fsp, sw), cscale(Fse, omc_G0)));
+            if (a.filter) {
+                const T rx = (T)col / (T)a.hx;
+                const T rz = (T)(mz < 0 ? -mz : mz) / (T)(NZ / 2);
+                const T A = (T)0.125 * ((T)5 + (T)4 * d_cospi(rx) - d_cospi((T)2 * rx)) *
+                            ((T)0.125 * ((T)5 + (T)4 * d_cospi(rz) - d_cospi((T)2 * rz)));
+                e1 = cscale(e1, A);
+                p1 = cscale(p1, A);
             }
+            a.y_eta[idx] = e1;
+            a.y_psi[idx] = p1;
+        } break;
+        case FIN_RHS:
+            a.ko_eta[idx] = de; a.ko_psi[idx] = dp;
+            break;
+        case FIN_RK1: {
+            a.ka_eta[idx] = de; a.ka_psi[idx] = dp;
+            const T hd = (T)0.5 * a.dt;
+            a.ys_eta[idx] = cadd(a.y_eta[idx], cscale(de, hd));
+            a.ys_psi[idx] = cadd(a.y_psi[idx], cscale(dp, hd));
+        } break;
+        case FIN_RK2:
+        case FIN_RK3: {
+            a.ka_eta[idx] = cadd(a.ka_eta[idx], cscale(de, (T)2));
+            a.ka_psi[idx] = cadd(a.ka_psi[idx], cscale(dp, (T)2));
+            const T hd = a.mode == FIN_RK2 ? (T)0.5 * a.dt : a.dt;
+            a.ys_eta[idx] = cadd(a.y_eta[idx], cscale(de, hd));
+            a.ys_psi[idx] = cadd(a.y_psi[idx], cscale(dp, hd));
+        } break;
+        case FIN_RK4: {
+            const T w = a.dt / (T)6;
+            T A = 1;
+            if (a.filter) {
+                const T rx = (T)col / (T)a.hx;
+                const T rz = (T)(mz < 0 ? -mz : mz) / (T)(NZ / 2);
+                A = (T)0.125 * ((T)5 + (T)4 * d_cospi(rx) - d_cospi((T)2 * rx)) *
+                    ((T)0.125 * ((T)5 + (T)4 * d_cospi(rz) - d_cospi((T)2 * rz)));
+            }
+            const cx<T> ye = cadd(a.y_eta[idx], cscale(cadd(a.ka_eta[idx], de), w));
+            const cx<T> yp = cadd(a.y_psi[idx], cscale(cadd(a.ka_psi[idx], dp), w));
+            a.y_eta[idx] = cscale(ye, A);
+            a.y_psi[idx] = cscale(yp, A);
+        } break;
+        case FIN_ENERGY: {
+            const double wgt = col == 0 ? 1.0 : 2.0;
+            e_kin += wgt * ((double)sp.x * (double)de.x + (double)sp.y * (double)de.y);
+            e_pot += wgt * ((double)se.x * (double)se.x + (double)se.y * (double)se.y);
+            const bool fin = isfinite((double)se.x) && isfinite((double)se.y) &&
+                             isfinite((double)sp.x) && isfinite((double)sp.y);
+            if (!fin) e_bad += 1.0;
+        } break;
+        default: break;
         }
     }
     if (a.mode == FIN_ENERGY) {
