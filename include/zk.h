@@ -94,6 +94,24 @@ zk_status zk_rhs(zk_ctx *ctx, void *deta_dt, void *dpsi_dt, int dtype, int on_de
  * (mean set to zero). Synchronises. */
 zk_status zk_dno(zk_ctx *ctx, void *v, int dtype, int on_device);
 
+/* Inverse DNO map of Eq. 19 (Sec. 3.5): replace psi so that G(eta) psi = v at
+ * the current eta, for physical v [nz][nx]. psi(0) = G0^{-1} v, then `iters`
+ * fixed-point updates psi <- G0^{-1}(v - [G(eta) - G0] psi) (the paper uses 8);
+ * the k = 0 mode of psi (its mean, which G0 does not see) keeps its value.
+ * Used to start from a physically specified (eta, v) pair. Synchronises. */
+zk_status zk_dno_inverse(zk_ctx *ctx, const void *v, int dtype, int on_device, int iters);
+
+/* Relaxation source of Sec. 5 after a wave step (Alg. 2 steps 7-9): keep
+ * v = G(eta) psi of the current state, relax eta pointwise toward eta_target
+ * with rate sigma [nz][nx] (1/s) by the exact decay of Eq. 34,
+ * eta <- eta_t + (eta - eta_t) exp(-sigma dt), then recompute psi from the
+ * relaxed eta and v by the inverse map (Eq. 35 via Eq. 19, `iters` updates).
+ * sigma >= 0 and eta_target are physical arrays of the given dtype (a box
+ * footprint ramp as in Eq. 33 is the caller's choice). The IF-AB2 history is
+ * kept, as in the paper's substep loop. Synchronises. */
+zk_status zk_relax(zk_ctx *ctx, const void *sigma, const void *eta_target, int dtype, int on_device,
+                   double dt, int iters);
+
 /* Advance n steps of size dt with the selected integrator (each followed by
  * the state filter when enabled). Asynchronous on the context's stream; the
  * launch sequence of one step is captured once in a CUDA graph and replayed.

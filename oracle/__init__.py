@@ -6,4 +6,4 @@ never imports it and the two share no code (only the seeded input generators
 of ``paper_2608_25203_b300.seas`` feed both, as data).
 """
 from .dft import dft, dft_matrix, fwd2, inv2  # noqa: F401
-from .zakharov import Grid, Oracle, mode_index, padded_size, run  # noqa: F401
+from .zakharov import Grid, Oracle, mode_index, padded_size, run, sigma_box  # noqa: F401

@@ -281,6 +281,42 @@ class Oracle:
         c, sw, G0sw, gsw, _, _ = self.if_coeffs(dt)
         return c * eh + G0sw * ph, -gsw * eh + c * ph
 
+    # ---- state recovery and the relaxation source (Secs. 3.5 and 5) -----------
+    def dno_inverse(self, eh: np.ndarray, vh: np.ndarray, iters: int = 8, ph0: np.ndarray = None):
+        """Inverse DNO map of Eq. 19 by fixed-point iteration.
+
+        psi(0) = G0^{-1} v, psi(n+1) = G0^{-1}(v - [G(eta) - G0] psi(n)), where
+        G(eta) - G0 is the same truncated, tapered nonlinear part as in the
+        right-hand side (all retained orders, each weighted by eps^m). G0 has
+        no inverse on the k = 0 mode; that mode of psi is taken from ph0
+        (reading: the mean potential is kept), else zero.
+        """
+        gr = self.gr
+        G0 = gr.G0
+        inv = np.where(G0 > 0, 1.0 / np.where(G0 > 0, G0, 1.0), 0.0)
+        mean = ph0[0, 0] if ph0 is not None else 0.0
+        ph = vh * inv
+        ph[0, 0] = mean
+        for _ in range(iters):
+            nl = self.dno(eh, ph) - G0 * ph
+            nl[0, 0] = 0.0
+            ph = (vh - nl) * inv
+            ph[0, 0] = mean
+        return ph
+
+    def relax(self, eh: np.ndarray, ph: np.ndarray, dt: float, sigma: np.ndarray, eta_target: np.ndarray,
+              iters: int = 8):
+        """Eq. 34 then Eq. 35 after a wave step (the splitting of Sec. 5.3, Alg. 2 steps 7-9).
+
+        v = G(eta) psi at the post-step state; eta <- eta_t + (eta - eta_t) exp(-sigma dt)
+        pointwise in physical space; psi <- G(eta_relaxed)^{-1} v.
+        """
+        vh = self.dno(eh, ph)
+        eta = self.physical(eh)
+        eta_r = eta_target + (eta - eta_target) * np.exp(-sigma * dt)
+        eh_r = self.spectrum(eta_r)
+        return eh_r, self.dno_inverse(eh_r, vh, iters=iters, ph0=ph)
+
     # ---- diagnostics ----------------------------------------------------------
     def energy(self, eh: np.ndarray, ph: np.ndarray):
         """Hamiltonian of Eq. 1 by Parseval: returns (H, kinetic, potential, mean_eta)."""
@@ -340,6 +376,24 @@ def run(oracle: Oracle, eta: np.ndarray, psi: np.ndarray, dt: float, nsteps: int
         if callback is not None:
             callback(n + 1, eh, ph)
     return oracle.physical(eh), oracle.physical(ph)
+
+
+def sigma_box(gr: Grid, x0: float, x1: float, z0: float, z1: float, wb: float, sigma_max: float):
+    """Relaxation rate of Eq. 33 on an axis-aligned box footprint.
+
+    sigma = sigma_max * rho(dist / wb) inside the box, 0 outside, with dist the
+    distance to the nearest box edge and rho the cubic smoothstep
+    rho(s) = 3 s^2 - 2 s^3 on [0, 1], clamped to 1 beyond (reading: the paper
+    asks only for a smooth ramp with rho(0) = 0 and rho(1) = 1).
+    """
+    x = np.arange(gr.nx) * gr.dx
+    z = np.arange(gr.nz) * gr.dz
+    Z, X = np.meshgrid(z, x, indexing="ij")
+    inside = (X >= x0) & (X <= x1) & (Z >= z0) & (Z <= z1)
+    dist = np.minimum(np.minimum(X - x0, x1 - X), np.minimum(Z - z0, z1 - Z))
+    s = np.clip(dist / wb, 0.0, 1.0)
+    rho = s * s * (3.0 - 2.0 * s)
+    return np.where(inside, sigma_max * rho, 0.0)
 
 
 def factorial_table(M: int):

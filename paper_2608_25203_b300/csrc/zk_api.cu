@@ -259,6 +259,20 @@ cudaError_t launch_cols_t(cx<T>* f0, cx<T>* f1, int hx, const cx<T>* tw, cudaStr
     return cudaGetLastError();
 }
 
+template <typename T, typename TIN, int NX>
+cudaError_t launch_relax_rows_t(cx<T>* f, const void* sigma, const void* target, int nz, T dt, T scale,
+                                const cx<T>* tw, cudaStream_t s) {
+    constexpr int TL = Plan<NX>::TL;
+    const int threads = TL >= 128 ? TL : 128;
+    const int rows = threads / TL;
+    const size_t smem = (size_t)rows * line_stride(NX) * sizeof(cx<T>);
+    cudaError_t e = ensure_smem((const void*)relax_rows_kernel<T, TIN, NX>, smem);
+    if (e != cudaSuccess) return e;
+    relax_rows_kernel<T, TIN, NX><<<(nz + rows - 1) / rows, threads, smem, s>>>(
+        f, (const TIN*)sigma, (const TIN*)target, nz, dt, scale, tw);
+    return cudaGetLastError();
+}
+
 #define ZK_SWITCH_N(n, CALL)                                     \
     switch (n) {                                                 \
     case 16: { constexpr int N_ = 16; return CALL; }             \
@@ -279,6 +293,11 @@ cudaError_t launch_rows_fwd(int nx, const void* fa, const void* fb, int nz, cx<T
 template <typename T, typename TOUT>
 cudaError_t launch_rows_inv(int nx, const cx<T>* ia, const cx<T>* ib, int nz, T scale, void* fa, void* fb, const cx<T>* tw, cudaStream_t s) {
     ZK_SWITCH_N(nx, (launch_rows_inv_t<T, TOUT, N_>(ia, ib, nz, scale, fa, fb, tw, s)))
+}
+template <typename T, typename TIN>
+cudaError_t launch_relax_rows(int nx, cx<T>* f, const void* sigma, const void* target, int nz, T dt, T scale,
+                              const cx<T>* tw, cudaStream_t s) {
+    ZK_SWITCH_N(nx, (launch_relax_rows_t<T, TIN, N_>(f, sigma, target, nz, dt, scale, tw, s)))
 }
 template <typename T, bool INV>
 cudaError_t launch_cols(int nz, cx<T>* f0, cx<T>* f1, int hx, const cx<T>* tw, cudaStream_t s) {
@@ -491,6 +510,40 @@ struct Pipe {
         fin.y_eta = C(c->y_eta); fin.y_psi = C(c->y_psi);
         fin.h_eta = C(c->h_eta); fin.h_psi = C(c->h_psi);
         return rhs(c, C(c->y_eta), C(c->y_psi), fin, s, nlaunch);
+    }
+
+    // Eq. 19: psi from v_hat at the current eta, `iters` fixed-point updates after psi = v/G0.
+    static cudaError_t dno_inverse(zk_ctx* c, const cx<T>* vhat, int iters, cudaStream_t s) {
+        const int n = c->nz * c->hx;
+        inv_g0_kernel<T><<<(n + 255) / 256, 256, 0, s>>>(vhat, C(c->y_psi), c->nz, c->hx,
+                                                         (T)(2.0 * M_PI / c->Lx), (T)(2.0 * M_PI / c->Lz), (T)c->h);
+        cudaError_t e = cudaGetLastError();
+        for (int it = 0; it < iters && e == cudaSuccess; ++it) {
+            ColArgs<T> fin = col_base(c);
+            fin.mode = FIN_INVDNO;
+            fin.y_psi = C(c->y_psi);
+            fin.v_hat = vhat;
+            e = rhs(c, C(c->y_eta), C(c->y_psi), fin, s, nullptr);
+        }
+        return e;
+    }
+
+    // Eq. 34 on eta (physical, pointwise), through the ko_psi scratch spectrum.
+    static cudaError_t relax_eta(zk_ctx* c, const void* sigma, const void* target, int dtype, double dt,
+                                 cudaStream_t s) {
+        const cx<T>* twx = reinterpret_cast<const cx<T>*>(c->tw_x);
+        const cx<T>* twz = reinterpret_cast<const cx<T>*>(c->tw_z);
+        const size_t compact = (size_t)c->nz * c->hx * sizeof(cx<T>);
+        cx<T>* f = C(c->ko_psi);
+        cudaError_t e = cudaMemcpyAsync(f, c->y_eta, compact, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = launch_cols<T, true>(c->nz, f, nullptr, c->hx, twz, s);
+        const T scale = (T)(1.0 / ((double)c->nx * c->nz));
+        if (e == cudaSuccess)
+            e = dtype == ZK_F32 ? launch_relax_rows<T, float>(c->nx, f, sigma, target, c->nz, (T)dt, scale, twx, s)
+                                : launch_relax_rows<T, double>(c->nx, f, sigma, target, c->nz, (T)dt, scale, twx, s);
+        if (e == cudaSuccess) e = launch_cols<T, false>(c->nz, f, nullptr, c->hx, twz, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(c->y_eta, f, compact, cudaMemcpyDeviceToDevice, s);
+        return e;
     }
 
     static cudaError_t rhs_out(zk_ctx* c, cudaStream_t s) {
@@ -784,6 +837,54 @@ zk_status zk_dno(zk_ctx* c, void* v, int dtype, int on_device) {
     cudaError_t e = c->prec == ZK_F32 ? Pipe<float>::rhs_out(c, user_stream(c)) : Pipe<double>::rhs_out(c, user_stream(c));
     if (e != cudaSuccess) return ZK_ECUDA;
     return out_physical(c, c->ko_eta, nullptr, v, nullptr, dtype, on_device);
+}
+
+zk_status zk_dno_inverse(zk_ctx* c, const void* v, int dtype, int on_device, int iters) {
+    if (!c || !v || (dtype != ZK_F32 && dtype != ZK_F64) || iters < 0) return ZK_EINVAL;
+    if (!c->has_state) return ZK_ESTATE;
+    const void *dv, *dv2;
+    zk_status st = stage_in(c, v, v, dtype, on_device, &dv, &dv2);
+    if (st != ZK_OK) return st;
+    cudaStream_t s = user_stream(c);
+    cudaError_t e;
+    if (c->prec == ZK_F32) {
+        auto* ve = (cx<float>*)c->ko_eta;
+        e = dtype == ZK_F32
+            ? launch_rows_fwd<float, float>(c->nx, dv, dv, c->nz, ve, (cx<float>*)c->ko_psi, (const cx<float>*)c->tw_x, s)
+            : launch_rows_fwd<float, double>(c->nx, dv, dv, c->nz, ve, (cx<float>*)c->ko_psi, (const cx<float>*)c->tw_x, s);
+        if (e == cudaSuccess) e = launch_cols<float, false>(c->nz, ve, nullptr, c->hx, (const cx<float>*)c->tw_z, s);
+        if (e == cudaSuccess) e = Pipe<float>::dno_inverse(c, ve, iters, s);
+    } else {
+        auto* ve = (cx<double>*)c->ko_eta;
+        e = dtype == ZK_F32
+            ? launch_rows_fwd<double, float>(c->nx, dv, dv, c->nz, ve, (cx<double>*)c->ko_psi, (const cx<double>*)c->tw_x, s)
+            : launch_rows_fwd<double, double>(c->nx, dv, dv, c->nz, ve, (cx<double>*)c->ko_psi, (const cx<double>*)c->tw_x, s);
+        if (e == cudaSuccess) e = launch_cols<double, false>(c->nz, ve, nullptr, c->hx, (const cx<double>*)c->tw_z, s);
+        if (e == cudaSuccess) e = Pipe<double>::dno_inverse(c, ve, iters, s);
+    }
+    if (e != cudaSuccess) return ZK_ECUDA;
+    return cu(cudaStreamSynchronize(s));
+}
+
+zk_status zk_relax(zk_ctx* c, const void* sigma, const void* eta_target, int dtype, int on_device, double dt, int iters) {
+    if (!c || !sigma || !eta_target || (dtype != ZK_F32 && dtype != ZK_F64) || iters < 0 || !(dt >= 0)) return ZK_EINVAL;
+    if (!c->has_state) return ZK_ESTATE;
+    const void *ds, *dtg;
+    zk_status st = stage_in(c, sigma, eta_target, dtype, on_device, &ds, &dtg);
+    if (st != ZK_OK) return st;
+    cudaStream_t s = user_stream(c);
+    cudaError_t e;
+    if (c->prec == ZK_F32) {
+        e = Pipe<float>::rhs_out(c, s);                                  // v = G(eta) psi into ko_eta
+        if (e == cudaSuccess) e = Pipe<float>::relax_eta(c, ds, dtg, dtype, dt, s);
+        if (e == cudaSuccess) e = Pipe<float>::dno_inverse(c, (const cx<float>*)c->ko_eta, iters, s);
+    } else {
+        e = Pipe<double>::rhs_out(c, s);
+        if (e == cudaSuccess) e = Pipe<double>::relax_eta(c, ds, dtg, dtype, dt, s);
+        if (e == cudaSuccess) e = Pipe<double>::dno_inverse(c, (const cx<double>*)c->ko_eta, iters, s);
+    }
+    if (e != cudaSuccess) return ZK_ECUDA;
+    return cu(cudaStreamSynchronize(s));
 }
 
 zk_status zk_step(zk_ctx* c, double dt, int n) {

@@ -198,7 +198,8 @@ __global__ void __launch_bounds__(512) row_round_kernel(const RowArgs<T> a, cons
 // ---------------------------------------------------------------------------
 enum ColKind { COL_FROM_STATE = 0, COL_PHI = 1, COL_FINAL = 2 };
 enum ColSym { SYM_ID = 0, SYM_DZ = 1, SYM_ZA = 2 };
-enum FinalMode { FIN_RHS = 0, FIN_RK1 = 1, FIN_RK2 = 2, FIN_RK3 = 3, FIN_RK4 = 4, FIN_ENERGY = 5, FIN_IFAB2 = 6 };
+enum FinalMode { FIN_RHS = 0, FIN_RK1 = 1, FIN_RK2 = 2, FIN_RK3 = 3, FIN_RK4 = 4, FIN_ENERGY = 5, FIN_IFAB2 = 6,
+                 FIN_INVDNO = 7 };
 
 template <typename T>
 struct ColArgs {
@@ -229,6 +230,7 @@ struct ColArgs {
     int nx_grid;
     double* partial;          // energy: [gridDim.x][3]
     cx<T>* h_eta; cx<T>* h_psi;     // IF-AB2: nonlinear forcing of the previous step
+    const cx<T>* v_hat;             // inverse DNO: target v = G(eta) psi (compact)
     int ab_first;                   // IF-AB2: 1 = bootstrap with IF-Euler (F* = F_n)
 };
 
@@ -576,6 +578,70 @@ __global__ void cols_kernel(cx<T>* f0, cx<T>* f1, int hx, const cx<T>* __restric
         }
         group_sync<TL>(bar);
     }
+}
+
+
+// psi_hat = v_hat / G0 on every mode but k = 0 (first iterate of Eq. 19); the z
+// Nyquist row is set to zero, the k = 0 mode of psi is left as it is.
+template <typename T>
+__global__ void inv_g0_kernel(const cx<T>* __restrict__ v, cx<T>* __restrict__ psi, int nz, int hx,
+                              T kx0, T kz0, T h) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nz * hx) return;
+    const int ic = i / hx, col = i - ic * hx;
+    if (ic == nz / 2) { psi[i] = mk<T>(0, 0); return; }
+    if (ic == 0 && col == 0) return;
+    const int mz = ic < nz / 2 ? ic : ic - nz;
+    const T kx = kx0 * (T)col, kz = kz0 * (T)mz;
+    const T k = d_sqrt(kx * kx + kz * kz);
+    const T G0 = k * d_tanh(k * h);
+    psi[i] = cscale(v[i], (T)1 / G0);
+}
+
+// One row of a compact field (after its inverse column transform): inverse row
+// FFT to the physical row, eta <- eta_t + (eta - eta_t) exp(-sigma dt)
+// (Eq. 34), forward row FFT back to the half spectrum, in place.
+template <typename T, typename TIN, int NX>
+__global__ void relax_rows_kernel(cx<T>* __restrict__ f, const TIN* __restrict__ sigma,
+                                  const TIN* __restrict__ target, int nz, T dt, T scale,
+                                  const cx<T>* __restrict__ tw) {
+    using P = Plan<NX>;
+    constexpr int TL = P::TL;
+    constexpr int LS = line_stride(NX);
+    constexpr int HX = NX / 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int g = threadIdx.x / TL, lt = threadIdx.x % TL;
+    const int bar = 1 + (g & 7);
+    cx<T>* line = reinterpret_cast<cx<T>*>(smem_raw) + (size_t)g * LS;
+    const int z = blockIdx.x * (blockDim.x / TL) + g;
+    const bool valid = z < nz;
+    const int zz = valid ? z : 0;
+    for (int m = lt; m < NX; m += TL) {
+        int mm = -1;
+        bool mir = false;
+        if (m < HX) mm = m;
+        else if (m > NX - HX) { mm = NX - m; mir = true; }
+        cx<T> v = mk<T>(0, 0);
+        if (mm >= 0) {
+            cx<T> A = f[(long long)zz * HX + mm];
+            if (mm == 0) A.y = 0;
+            v = mir ? cconj(A) : A;
+        }
+        line[pidx(m)] = v;
+    }
+    group_sync<TL>(bar);
+    P::template run<true, T>(line, tw, lt, bar);
+    for (int p = lt; p < NX; p += TL) {
+        const long long gi = (long long)zz * NX + p;
+        const T e = line[pidx(p)].x * scale;
+        const T t = (T)target[gi];
+        const T r = t + (e - t) * d_exp(-(T)sigma[gi] * dt);
+        line[pidx(p)] = mk<T>(r, 0);
+    }
+    group_sync<TL>(bar);
+    P::template run<false, T>(line, tw, lt, bar);
+    if (valid)
+        for (int k = lt; k < HX; k += TL) f[(long long)z * HX + k] = line[pidx(k)];
 }
 
 }  // namespace zk

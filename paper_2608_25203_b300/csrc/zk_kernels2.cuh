@@ -313,6 +313,10 @@ col2_kernel(const ColArgs<T> a, const cx<T>* __restrict__ tw) {
         if (col == 0 && mz == 0) de = mk<T>(0, 0);
         const cx<T> dp = cadd(cscale(se, -a.g), Fp);
         switch (a.mode) {
+        case FIN_INVDNO: {
+            // Eq. 19: psi <- G0^{-1} (v - [G(eta) - G0] psi); the k = 0 mode keeps its value
+            if (!(col == 0 && mz == 0)) a.y_psi[idx] = cscale(csub(a.v_hat[idx], Fe), (T)1 / G0);
+        } break;
         case FIN_IFAB2: {
             // Eqs. 15-16: exact linear rotation plus the Duhamel response to the
             // AB2-extrapolated forcing F* (IF-Euler at the first step).

@@ -25,7 +25,8 @@ ZK_RK4, ZK_IFAB2 = 0, 1
 EXPORTS = [
     "zk_create", "zk_destroy", "zk_set_options", "zk_get_options", "zk_set_state", "zk_get_state",
     "zk_rhs", "zk_dno", "zk_step", "zk_energy", "zk_sync", "zk_device_bytes",
-    "zk_launches_per_step", "zk_profile_step", "zk_dno_static", "zk_strerror", "zk_version",
+    "zk_launches_per_step", "zk_profile_step", "zk_dno_static", "zk_dno_inverse", "zk_relax",
+    "zk_strerror", "zk_version",
 ]
 
 KERNEL_CLASSES = {0: "col_state", 1: "row_round", 2: "col_phi", 3: "row_final", 4: "col_final"}
@@ -71,6 +72,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "zk_launches_per_step": ([vp, ctypes.POINTER(i)], i),
         "zk_profile_step": ([vp, d, i, pd, ctypes.POINTER(i), pd, i, ctypes.POINTER(i)], i),
         "zk_dno_static": ([vp, vp, vp, i, i, d, d, d, d, i, d, i, vp], i),
+        "zk_dno_inverse": ([vp, vp, i, i, i], i),
+        "zk_relax": ([vp, vp, vp, i, i, d, i], i),
         "zk_strerror": ([i], ctypes.c_char_p),
         "zk_version": ([], ctypes.c_char_p),
     }
@@ -192,6 +195,21 @@ def zk_profile_step(ctx, dt, nsteps=1, cap=256):
     return list(ms[:k]), [KERNEL_CLASSES[x] for x in kind[:k]], list(by[:k])
 
 
+def zk_dno_inverse(ctx, v, iters=8, dtype=None):
+    dt = dtype if dtype is not None else _dtype_of(v)
+    pv, dv = _ptr(v, dt)
+    _check("zk_dno_inverse", load().zk_dno_inverse(ctx, pv, dt, dv, int(iters)))
+
+
+def zk_relax(ctx, sigma, eta_target, dt, iters=8, dtype=None):
+    d = dtype if dtype is not None else _dtype_of(sigma)
+    ps, ds = _ptr(sigma, d)
+    pt, dtg = _ptr(eta_target, d)
+    if ds != dtg:
+        raise ValueError("sigma and eta_target must both be host or both device arrays")
+    _check("zk_relax", load().zk_relax(ctx, ps, pt, d, ds, float(dt), int(iters)))
+
+
 def zk_dno_static(eta, psi, v, Lx, Lz, h, g=9.81, M=5, eps=1.0, taper=1, stream=None):
     """G(eta) psi into v with no device allocation (scratch is a fixed array in the library).
 
@@ -265,6 +283,15 @@ class Zakharov:
 
     def step(self, dt, n=1):
         zk_step(self.ctx, dt, n)
+
+    def dno_inverse(self, v, iters=8):
+        zk_dno_inverse(self.ctx, np.ascontiguousarray(v) if isinstance(v, np.ndarray) else v, iters)
+
+    def relax(self, sigma, eta_target, dt, iters=8):
+        if isinstance(sigma, np.ndarray):
+            sigma = np.ascontiguousarray(sigma)
+            eta_target = np.ascontiguousarray(eta_target, dtype=sigma.dtype)
+        zk_relax(self.ctx, sigma, eta_target, dt, iters)
 
     def energy(self):
         return zk_energy(self.ctx)
