@@ -19,6 +19,13 @@ sampled during the timed region, and the FP64 oracle timed on this host.
 
 --impl reference: the FP64 CPU oracle, timed on the host cores on samples of
 the same workload (rank 0 only).
+
+--workload tank: the closed 20 m x 20 m tank of the wave-propagation runtime
+comparison (Sec. 5, Table 3): 128 x 128 tank cells, reflecting walls by even
+extension to a 256 x 256 computational grid (Sec. 3.3), Gaussian bump at rest
+(A = 2 m at h = 20 m, A = 1 m at h = 1 m, sigma = 1 m, R = 6 m), eps = 1,
+IF-AB2 at dt = 0.01 s, orders 2 and 3, 2000 frames each. Prints one JSON line
+with ms per step for each case; the paper's RTX 4090 times are context only.
 """
 from __future__ import annotations
 
@@ -162,6 +169,52 @@ def reference_arm(args):
     return 0
 
 
+TANK_PAPER_MS = {(20.0, 2): 6.352, (1.0, 2): 6.167, (20.0, 3): 13.52, (1.0, 3): 13.43}
+
+
+def tank_arm(args):
+    """Per-step time of the closed-tank runs (Table 3 setting) through the graph-replayed IF-AB2 step."""
+    import numpy as np
+    import torch
+
+    from paper_2608_25203_b300 import seas
+    from paper_2608_25203_b300 import zk
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    stream = torch.cuda.current_stream()
+    m, L, dt, frames = 128, 20.0, 0.01, args.frames
+    cases = []
+    for h, A in ((20.0, 2.0), (1.0, 1.0)):
+        for M in (2, 3):
+            eta, psi = seas.gaussian_bump(m, m, L, L, A)
+            sim = zk.Zakharov(2 * m, 2 * m, 2 * L, 2 * L, h, 9.81, M, zk.ZK_F32, eps=1.0, stream=stream.cuda_stream)
+            zk.zk_set_options(sim.ctx, eps=1.0, integrator=zk.ZK_IFAB2, stream=stream.cuda_stream)
+            zk.zk_set_state_tank(sim.ctx, eta.astype(np.float32), psi.astype(np.float32))
+            sim.step(dt, max(3, args.warmup))
+            torch.cuda.synchronize()
+            t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
+            sim.step(dt, frames)
+            t1.record(stream)
+            torch.cuda.synchronize()
+            ms = t0.elapsed_time(t1) / frames
+            te = np.empty((m, m), np.float32)
+            tp = np.empty((m, m), np.float32)
+            zk.zk_get_state_tank(sim.ctx, te, tp)
+            cases.append({"h": h, "A": A, "M": M, "ms_per_step": ms, "paper_rtx4090_ms": TANK_PAPER_MS[(h, M)],
+                          "launches_per_step": zk.zk_launches_per_step(sim.ctx),
+                          "state_finite": bool(np.isfinite(te).all() and np.isfinite(tp).all()),
+                          "max_eta": float(np.abs(te).max())})
+            sim.close()
+    worst = max(c["ms_per_step"] for c in cases)
+    print(json.dumps({"metric": "closed-tank step time (Table 3 setting)", "value": worst, "unit": "ms/step",
+                      "higher_is_better": False, "steps": frames, "dtype": "f32", "data": "synthetic",
+                      "config": {"workload": "20 m tank, 128^2 cells, even extension to 256^2, Gaussian bump, "
+                                             "eps=1, IF-AB2 dt=0.01 s, M=2,3, h=20 m and 1 m"},
+                      "cases": cases}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -171,7 +224,11 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--profile-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="sea", choices=["sea", "tank"])
+    ap.add_argument("--frames", type=int, default=2000, help="timed steps per case of --workload tank")
     args = ap.parse_args()
+    if args.workload == "tank":
+        return tank_arm(args)
     if args.impl == "reference":
         return reference_arm(args)
     if args.warmup < 3:

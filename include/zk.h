@@ -94,6 +94,16 @@ zk_status zk_rhs(zk_ctx *ctx, void *deta_dt, void *dpsi_dt, int dtype, int on_de
  * (mean set to zero). Synchronises. */
 zk_status zk_dno(zk_ctx *ctx, void *v, int dtype, int on_device);
 
+/* Reflecting walls by even extension (Sec. 3.3, Eq. 12). The context's grid
+ * (nx, nz, Lx, Lz) is the doubled computational grid; the caller's arrays are
+ * the tank of (nx/2) x (nz/2) cell-centred samples over Lx/2 x Lz/2. set mirrors
+ * the tank across each wall (sample i -> 2m-1-i) into the doubled periodic
+ * field; the even symmetry is kept by every step (all operators commute with
+ * the reflection), so get returns the (0:nz/2, 0:nx/2) corner. set resets the
+ * integrator history like zk_set_state; get synchronises. */
+zk_status zk_set_state_tank(zk_ctx *ctx, const void *eta, const void *psi, int dtype, int on_device);
+zk_status zk_get_state_tank(zk_ctx *ctx, void *eta, void *psi, int dtype, int on_device);
+
 /* Inverse DNO map of Eq. 19 (Sec. 3.5): replace psi so that G(eta) psi = v at
  * the current eta, for physical v [nz][nx]. psi(0) = G0^{-1} v, then `iters`
  * fixed-point updates psi <- G0^{-1}(v - [G(eta) - G0] psi) (the paper uses 8);

@@ -89,6 +89,7 @@ struct zk_ctx {
     long long fstride = 0;
     void *acc = nullptr;
     void *stage = nullptr;
+    void *tank = nullptr;      // two (nx/2) x (nz/2) FP64-sized arrays for tank I/O
     double *partial = nullptr;
     int npartial = 0;
     double *esum = nullptr;
@@ -757,6 +758,7 @@ zk_status zk_create(zk_ctx** out, int nx, int nz, double Lx, double Lz, double h
     if (st == ZK_OK) st = dalloc(c, &c->col, (size_t)c->nfields * c->fstride * c->csz);
     if (st == ZK_OK) st = dalloc(c, &c->acc, (size_t)c->npz * c->npx * rsz);
     if (st == ZK_OK) st = dalloc(c, &c->stage, (size_t)2 * nx * nz * kIoElem);
+    if (st == ZK_OK) st = dalloc(c, &c->tank, (size_t)2 * (nx / 2) * (nz / 2) * 8);
     c->npartial = col_grid(c->npz, c->hx);
     if (st == ZK_OK) st = dalloc(c, (void**)&c->partial, (size_t)3 * c->npartial * sizeof(double));
     if (st == ZK_OK) st = dalloc(c, (void**)&c->esum, 4 * sizeof(double));
@@ -837,6 +839,62 @@ zk_status zk_dno(zk_ctx* c, void* v, int dtype, int on_device) {
     cudaError_t e = c->prec == ZK_F32 ? Pipe<float>::rhs_out(c, user_stream(c)) : Pipe<double>::rhs_out(c, user_stream(c));
     if (e != cudaSuccess) return ZK_ECUDA;
     return out_physical(c, c->ko_eta, nullptr, v, nullptr, dtype, on_device);
+}
+
+// Tank (walled) I/O through the even extension (Sec. 3.3): the context's grid is
+// the doubled one; the caller's arrays are the (nx/2) x (nz/2) tank. Tank copies
+// go to their own buffer (c->tank, two FP64-sized tank arrays); the extended
+// fields go to the two staging slots, so no copy overlaps another.
+zk_status zk_set_state_tank(zk_ctx* c, const void* eta, const void* psi, int dtype, int on_device) {
+    if (!c || !eta || !psi || (dtype != ZK_F32 && dtype != ZK_F64)) return ZK_EINVAL;
+    const int mx = c->nx / 2, mz = c->nz / 2;
+    const size_t es = dtype == ZK_F32 ? 4 : 8, tank = (size_t)mx * mz * es;
+    cudaStream_t s = user_stream(c);
+    char* te = (char*)c->tank;
+    char* tp = te + (size_t)mx * mz * 8;
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (cudaMemcpyAsync(te, eta, tank, k, s) != cudaSuccess) return ZK_ECUDA;
+    if (cudaMemcpyAsync(tp, psi, tank, k, s) != cudaSuccess) return ZK_ECUDA;
+    char* de = (char*)c->stage;
+    char* dp = de + (size_t)c->nx * c->nz * kIoElem;
+    const int blocks = 4 * 148, threads = 256;
+    if (dtype == ZK_F32) {
+        even_extend_kernel<float><<<blocks, threads, 0, s>>>((const float*)te, (float*)de, mx, mz);
+        even_extend_kernel<float><<<blocks, threads, 0, s>>>((const float*)tp, (float*)dp, mx, mz);
+    } else {
+        even_extend_kernel<double><<<blocks, threads, 0, s>>>((const double*)te, (double*)de, mx, mz);
+        even_extend_kernel<double><<<blocks, threads, 0, s>>>((const double*)tp, (double*)dp, mx, mz);
+    }
+    if (cudaGetLastError() != cudaSuccess) return ZK_ECUDA;
+    return zk_set_state(c, de, dp, dtype, 1);
+}
+
+zk_status zk_get_state_tank(zk_ctx* c, void* eta, void* psi, int dtype, int on_device) {
+    if (!c || !eta || !psi || (dtype != ZK_F32 && dtype != ZK_F64)) return ZK_EINVAL;
+    if (!c->has_state) return ZK_ESTATE;
+    const int mx = c->nx / 2, mz = c->nz / 2;
+    const size_t es = dtype == ZK_F32 ? 4 : 8;
+    cudaStream_t s = user_stream(c);
+    char* fe = (char*)c->stage;                                 // full doubled fields, device
+    char* fp = fe + (size_t)c->nx * c->nz * kIoElem;
+    zk_status r = zk_get_state(c, fe, fp, dtype, 1);
+    if (r != ZK_OK) return r;
+    if (on_device) {
+        const int blocks = 148, threads = 256;
+        if (dtype == ZK_F32) {
+            crop_kernel<float><<<blocks, threads, 0, s>>>((const float*)fe, (float*)eta, mx, mz);
+            crop_kernel<float><<<blocks, threads, 0, s>>>((const float*)fp, (float*)psi, mx, mz);
+        } else {
+            crop_kernel<double><<<blocks, threads, 0, s>>>((const double*)fe, (double*)eta, mx, mz);
+            crop_kernel<double><<<blocks, threads, 0, s>>>((const double*)fp, (double*)psi, mx, mz);
+        }
+        if (cudaGetLastError() != cudaSuccess) return ZK_ECUDA;
+    } else {
+        const size_t row = (size_t)mx * es, pitch = (size_t)2 * mx * es;
+        if (cudaMemcpy2DAsync(eta, row, fe, pitch, row, mz, cudaMemcpyDeviceToHost, s) != cudaSuccess) return ZK_ECUDA;
+        if (cudaMemcpy2DAsync(psi, row, fp, pitch, row, mz, cudaMemcpyDeviceToHost, s) != cudaSuccess) return ZK_ECUDA;
+    }
+    return cu(cudaStreamSynchronize(s));
 }
 
 zk_status zk_dno_inverse(zk_ctx* c, const void* v, int dtype, int on_device, int iters) {

@@ -644,4 +644,30 @@ __global__ void relax_rows_kernel(cx<T>* __restrict__ f, const TIN* __restrict__
         for (int k = lt; k < HX; k += TL) f[(long long)z * HX + k] = line[pidx(k)];
 }
 
+
+// Even extension across reflecting walls (Sec. 3.3, Eq. 12): a tank field of
+// mx x mz cell-centred samples becomes the (2mx) x (2mz) periodic field
+// f~(i, k) = f(r(i), r(k)) with r(i) = i for i < m, 2m - 1 - i otherwise.
+template <typename TIN>
+__global__ void even_extend_kernel(const TIN* __restrict__ src, TIN* __restrict__ dst, int mx, int mz) {
+    const int nx = 2 * mx;
+    const long long n = (long long)nx * 2 * mz;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(t / nx), i = (int)(t - (long long)k * nx);
+        const int si = i < mx ? i : nx - 1 - i;
+        const int sk = k < mz ? k : 2 * mz - 1 - k;
+        dst[t] = src[(long long)sk * mx + si];
+    }
+}
+
+// The (0:mz, 0:mx) corner of a (2mx) x (2mz) field.
+template <typename TIN>
+__global__ void crop_kernel(const TIN* __restrict__ src, TIN* __restrict__ dst, int mx, int mz) {
+    const long long n = (long long)mx * mz;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(t / mx), i = (int)(t - (long long)k * mx);
+        dst[t] = src[(long long)k * 2 * mx + i];
+    }
+}
+
 }  // namespace zk

@@ -26,6 +26,7 @@ EXPORTS = [
     "zk_create", "zk_destroy", "zk_set_options", "zk_get_options", "zk_set_state", "zk_get_state",
     "zk_rhs", "zk_dno", "zk_step", "zk_energy", "zk_sync", "zk_device_bytes",
     "zk_launches_per_step", "zk_profile_step", "zk_dno_static", "zk_dno_inverse", "zk_relax",
+    "zk_set_state_tank", "zk_get_state_tank",
     "zk_strerror", "zk_version",
 ]
 
@@ -73,6 +74,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "zk_profile_step": ([vp, d, i, pd, ctypes.POINTER(i), pd, i, ctypes.POINTER(i)], i),
         "zk_dno_static": ([vp, vp, vp, i, i, d, d, d, d, i, d, i, vp], i),
         "zk_dno_inverse": ([vp, vp, i, i, i], i),
+        "zk_set_state_tank": ([vp, vp, vp, i, i], i),
+        "zk_get_state_tank": ([vp, vp, vp, i, i], i),
         "zk_relax": ([vp, vp, vp, i, i, d, i], i),
         "zk_strerror": ([i], ctypes.c_char_p),
         "zk_version": ([], ctypes.c_char_p),
@@ -193,6 +196,22 @@ def zk_profile_step(ctx, dt, nsteps=1, cap=256):
                                                      ctypes.byref(n)))
     k = n.value
     return list(ms[:k]), [KERNEL_CLASSES[x] for x in kind[:k]], list(by[:k])
+
+
+def zk_set_state_tank(ctx, eta, psi, dtype=None):
+    dt = dtype if dtype is not None else _dtype_of(eta)
+    pe, de = _ptr(eta, dt)
+    pp, dp = _ptr(psi, dt)
+    if de != dp:
+        raise ValueError("eta and psi must both be host or both device arrays")
+    _check("zk_set_state_tank", load().zk_set_state_tank(ctx, pe, pp, dt, de))
+
+
+def zk_get_state_tank(ctx, eta, psi, dtype=None):
+    dt = dtype if dtype is not None else _dtype_of(eta)
+    pe, de = _ptr(eta, dt)
+    pp, _ = _ptr(psi, dt)
+    _check("zk_get_state_tank", load().zk_get_state_tank(ctx, pe, pp, dt, de))
 
 
 def zk_dno_inverse(ctx, v, iters=8, dtype=None):
