@@ -26,6 +26,12 @@ extension to a 256 x 256 computational grid (Sec. 3.3), Gaussian bump at rest
 (A = 2 m at h = 20 m, A = 1 m at h = 1 m, sigma = 1 m, R = 6 m), eps = 1,
 IF-AB2 at dt = 0.01 s, orders 2 and 3, 2000 frames each. Prints one JSON line
 with ms per step for each case; the paper's RTX 4090 times are context only.
+
+--workload batch: 96 independent JONSWAP tiles at dx = 0.78125 m (40 x 128^2,
+32 x 256^2, 16 x 512^2, 8 x 1024^2), orders cycling 3..6, Hs, h, Tp drawn per
+tile (seeds 1000 + tile), eps = 0.5, RK4 dt = 0.02 s, 200 steps, FP32, all
+advanced by one graph per step. Timed with the default launch shapes and again
+after the autotuner; value = tile-steps/s after tuning.
 """
 from __future__ import annotations
 
@@ -182,7 +188,7 @@ def tank_arm(args):
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     stream = torch.cuda.current_stream()
-    m, L, dt, frames = 128, 20.0, 0.01, args.frames
+    m, L, dt, frames = 128, 20.0, 0.01, args.frames or 2000
     cases = []
     for h, A in ((20.0, 2.0), (1.0, 1.0)):
         for M in (2, 3):
@@ -215,6 +221,65 @@ def tank_arm(args):
     return 0
 
 
+def batch_arm(args):
+    """The mixed 96-tile batch: one captured graph per step, default vs autotuned launch shapes."""
+    import numpy as np
+    import torch
+
+    from paper_2608_25203_b300 import seas
+    from paper_2608_25203_b300 import zk
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    stream = torch.cuda.current_stream()
+    tiles = seas.batch_tiles()
+    steps = args.frames if args.frames else 200
+    dt, eps = 0.02, 0.5
+    b = zk.Batch(tiles, eps=eps, stream=stream.cuda_stream)
+    for i, t in enumerate(tiles):
+        e, p, _ = seas.jonswap_sea(t["nx"], t["nz"], t["Lx"], t["Lz"], t["h"], t["Hs"], t["Tp"], t["seed"])
+        b.set_state(i, e.astype(np.float32), p.astype(np.float32))
+    torch.cuda.synchronize()
+    ngroups, launches, nbytes = b.info()
+    cells = sum(t["nx"] * t["nz"] for t in tiles)
+
+    def timed(n):
+        b.step(dt, max(3, args.warmup))
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        b.step(dt, n)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        return t0.elapsed_time(t1) / n
+
+    ms_default = timed(steps)
+    cache = os.path.join(tempfile.mkdtemp(prefix="zk_tune_"), "tune.json")
+    t0 = time.time()
+    tuned, cached = b.autotune(dt, cache)
+    tune_s = time.time() - t0
+    ms_tuned = timed(steps)
+    finite = True
+    for i in range(len(tiles)):
+        try:
+            b.energy(i)
+        except zk.ZkError:
+            finite = False
+    groups = b.groups()
+    b.close()
+    print(json.dumps({
+        "metric": "batched tiles: tile-steps/s (96 mixed tiles, RK4)", "value": len(tiles) / (ms_tuned / 1e3),
+        "unit": "tile-steps/s", "higher_is_better": True, "steps": steps, "ms_per_step": ms_tuned,
+        "ms_per_step_default_shapes": ms_default, "cell_steps_per_s": cells / (ms_tuned / 1e3),
+        "dtype": "f32", "data": "synthetic", "n_gpus": 1,
+        "config": {"workload": "96 JONSWAP tiles dx=0.78125 m: 40x128^2, 32x256^2, 16x512^2, 8x1024^2; "
+                               "M cycling 3..6; eps=0.5; RK4 dt=0.02 s; FP32", "groups": ngroups,
+                   "launches_per_step": launches, "device_bytes": nbytes},
+        "autotune": {"groups_timed": tuned, "groups_cached": cached, "seconds": tune_s,
+                     "shapes": [{k: g[k] for k in ("nx", "M", "ntiles", "plan_v", "col_ci", "row_occ")} for g in groups]},
+        "state_finite": finite}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -224,11 +289,14 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--profile-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="sea", choices=["sea", "tank"])
-    ap.add_argument("--frames", type=int, default=2000, help="timed steps per case of --workload tank")
+    ap.add_argument("--workload", default="sea", choices=["sea", "tank", "batch"])
+    ap.add_argument("--frames", type=int, default=None,
+                    help="timed steps of --workload tank (default 2000 per case) or batch (default 200)")
     args = ap.parse_args()
     if args.workload == "tank":
         return tank_arm(args)
+    if args.workload == "batch":
+        return batch_arm(args)
     if args.impl == "reference":
         return reference_arm(args)
     if args.warmup < 3:

@@ -190,6 +190,58 @@ zk_status zk_dno_static(const float *eta, const float *psi, float *v, int nx, in
                         double Lx, double Lz, double h, double g, int M, double eps, int taper,
                         void *stream);
 
+/* ---- Batched tiles (many independent seas advanced together) ----
+ *
+ * A batch holds ntiles independent periodic tiles; tile t has grid
+ * nx[t] x nz[t] over Lx[t] x Lz[t], depth h[t] and order M[t] (limits as in
+ * zk_create), all with gravity g and one precision. Each tile is the same
+ * problem as a zk_ctx of its own (Sec. 3.2 right-hand side, Sec. 3.4 or RK4
+ * integration, Eq. 17 filter); the batch only changes how launches are made.
+ * Tiles with equal (nx, nz, Lx, Lz, M) form a group whose buffers are laid
+ * out tile after tile, and every pass of a group is one launch over all its
+ * tiles; zk_batch_step replays one captured graph in which the groups are
+ * independent branches, so the GPU runs the groups' launches concurrently.
+ * Results are bitwise equal to stepping each tile in its own context with the
+ * same launch shape (same kernels, same arithmetic order).
+ *
+ * Status: ZK_EINVAL for bad arguments or a tile index out of range;
+ * ZK_ESTATE when a tile without state is stepped, read or tuned; ZK_ENOMEM,
+ * ZK_ECUDA as elsewhere. The batch owns all its device memory. */
+typedef struct zk_batch zk_batch;
+zk_status zk_batch_create(zk_batch **out, int ntiles, const int *nx, const int *nz, const double *Lx,
+                          const double *Lz, const double *h, double g, const int *M, int precision);
+void zk_batch_destroy(zk_batch *b);
+/* Options for every tile (as zk_set_options); the stream is the batch's. */
+zk_status zk_batch_set_options(zk_batch *b, const zk_options *opt);
+/* Per-tile state I/O and energy: as zk_set_state / zk_get_state / zk_energy
+ * for tile `tile` (arrays [nz[tile]][nx[tile]]). Setting any tile's state
+ * restarts the IF-AB2 history of the whole batch (next step is IF-Euler). */
+zk_status zk_batch_set_state(zk_batch *b, int tile, const void *eta, const void *psi, int dtype, int on_device);
+zk_status zk_batch_get_state(zk_batch *b, int tile, void *eta, void *psi, int dtype, int on_device);
+zk_status zk_batch_energy(zk_batch *b, int tile, double *H, double *kin, double *pot, double *mean_eta);
+/* Advance every tile by n steps of dt, asynchronously on the batch stream. */
+zk_status zk_batch_step(zk_batch *b, double dt, int n);
+zk_status zk_batch_sync(zk_batch *b);
+/* Number of groups, kernel launches per step (all groups) and device bytes. */
+zk_status zk_batch_info(const zk_batch *b, int *ngroups, int *launches_per_step, size_t *device_bytes);
+/* Group gi: its grid, order, tile count and launch shape. The launch shape is
+ * plan_v (FFT plan variant of the padded lines: 0 = default radices, 1 = the
+ * radix-16 alternative of lines 768, 1536, 3072), col_ci (columns per column-
+ * kernel block: 0 / 1 / 2 = half / default / double; FP32 lines >= 192 only)
+ * and row_occ (row-kernel blocks per SM, 0 = all that fit). */
+zk_status zk_batch_group(const zk_batch *b, int gi, int *nx, int *nz, int *M, int *ntiles, int *plan_v,
+                         int *col_ci, int *row_occ);
+zk_status zk_batch_set_shape(zk_batch *b, int gi, int plan_v, int col_ci, int row_occ);
+/* Autotuner: for each group, time one step (mean of 3 after a warm-up) under
+ * every launch shape and keep the fastest; shapes that cannot launch are
+ * skipped. The tiles' states and IF-AB2 histories are restored afterwards
+ * (the next IF-AB2 step is IF-Euler). With cache_path non-NULL, a group whose
+ * key (device name, grid, order, precision, tile count) is in the JSON cache
+ * takes the stored shape without timing, and new results are written back.
+ * tuned / cached (may be NULL) receive how many groups were timed / looked up.
+ * Blocks until done. */
+zk_status zk_batch_autotune(zk_batch *b, double dt, const char *cache_path, int *tuned, int *cached);
+
 /* Static text for a status code. */
 const char *zk_strerror(zk_status s);
 

@@ -28,30 +28,45 @@ namespace {
 constexpr int kIoElem = 8;  // bytes per staging element (fits f32 and f64)
 
 // columns per column-kernel block: 4 for wide line groups, else enough for 128 (FP32) / 64 (FP64) threads
-template <int NPZ, int ES> constexpr int col_cb() { return IPlan<NPZ>::TL >= 64 ? 4 : ((ES == 8 ? 128 : 64) / IPlan<NPZ>::TL); }
+template <int NPZ, int ES, int V = 0> constexpr int col_cb() {
+    return IPlan<NPZ, V>::TL >= 64 ? 4 : ((ES == 8 ? 128 : 64) / IPlan<NPZ, V>::TL);
+}
+// autotuner choice ci of columns per block: 0 = half, 1 = default, 2 = double
+template <int NPZ, int ES, int V> constexpr int col_cb_pick(int ci) {
+    return ci == 0 ? (col_cb<NPZ, ES, V>() > 1 ? col_cb<NPZ, ES, V>() / 2 : 1)
+                   : (ci == 2 ? 2 * col_cb<NPZ, ES, V>() : col_cb<NPZ, ES, V>());
+}
 
-// Blocks of a persistent kernel: resident blocks per SM x SMs (cached per kernel shape).
+// Resident blocks per SM of a kernel shape, and the SM count (cached per shape).
 std::mutex g_occ_mu;
-std::unordered_map<std::string, int> g_occ;
-int persistent_grid(const void* fn, int threads, size_t smem, int work) {
+std::unordered_map<std::string, std::pair<int, int>> g_occ;
+void occupancy(const void* fn, int threads, size_t smem, int* per_sm, int* sms) {
     char key[96];
     snprintf(key, sizeof(key), "%p/%d/%zu", fn, threads, smem);
-    int per = 0;
     {
         std::lock_guard<std::mutex> lk(g_occ_mu);
         auto it = g_occ.find(key);
-        if (it != g_occ.end()) per = it->second;
+        if (it != g_occ.end()) { *per_sm = it->second.first; *sms = it->second.second; return; }
     }
-    if (per == 0) {
-        int dev = 0, sms = 0, nb = 0;
+    int dev = 0, n = 0, nb = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, smem);
+    *per_sm = std::max(1, nb);
+    *sms = std::max(1, n);
+    std::lock_guard<std::mutex> lk(g_occ_mu);
+    g_occ[key] = {*per_sm, *sms};
+}
+
+// Largest dynamic shared memory a block may opt in to on this device.
+int smem_optin() {
+    static int v = -1;
+    if (v < 0) {
+        int dev = 0;
         cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, smem);
-        per = std::max(1, nb) * std::max(1, sms);
-        std::lock_guard<std::mutex> lk(g_occ_mu);
-        g_occ[key] = per;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     }
-    return std::min(work, per);
+    return v;
 }
 
 std::mutex g_attr_mu;
@@ -79,6 +94,16 @@ struct zk_ctx {
     bool has_state = false;
     size_t csz = 0;  // bytes per complex element
     void *tw_x = nullptr, *tw_z = nullptr, *tw_px = nullptr, *tw_pz = nullptr;
+    void* tw_pv[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};   // padded plan tables [variant][x, z]
+    // tiles sharing this grid and order (a batch group; 1 for a plain context):
+    // buffers are [tile][...] with these element strides, depth per tile
+    int nb = 1;
+    long long tcol = 0, tst = 0, tacc = 0;
+    void* hb = nullptr;                    // device [nb] depths in the compute type (nb > 1)
+    std::vector<double> hv;                // host copy of the depths
+    // launch shape (set by the batch autotuner): plan variant, columns-per-block
+    // choice (0 / 1 / 2 = half / default / double), row blocks per SM (0 = all resident)
+    int plan_v = 0, col_ci = 1, row_occ = 0;
     void *y_eta = nullptr, *y_psi = nullptr, *ys_eta = nullptr, *ys_psi = nullptr;
     void *ka_eta = nullptr, *ka_psi = nullptr, *ko_eta = nullptr, *ko_psi = nullptr;
     void *h_eta = nullptr, *h_psi = nullptr;   // IF-AB2 forcing history
@@ -146,9 +171,9 @@ void make_twiddles(int n, std::vector<cx<T>>& out) {
 // ---------------------------------------------------------------------------
 // Launch helpers dispatched on the compile-time line lengths.
 // ---------------------------------------------------------------------------
-template <typename T, int NPX>
+template <typename T, int NPX, int V>
 cudaError_t launch_row_t(const RowArgs<T>& a, const cx<T>* tw, int npz, cudaStream_t s) {
-    constexpr int TL = IPlan<NPX>::TL;
+    constexpr int TL = IPlan<NPX, V>::TL;
     // narrow groups: one line per group, rounded to whole warps; wide groups:
     // at most 1024 threads, lines beyond that taken in waves
     int nl = a.nlines, groups;
@@ -156,73 +181,101 @@ cudaError_t launch_row_t(const RowArgs<T>& a, const cx<T>* tw, int npz, cudaStre
     else groups = std::min(nl, 1024 / TL);
     const int threads = groups * TL;
     const size_t smem = (size_t)nl * line_stride(NPX) * sizeof(cx<T>);
-    const void* fn = (const void*)row2_kernel<T, NPX>;
+    if (threads > 1024 || smem > (size_t)smem_optin()) return cudaErrorInvalidConfiguration;
+    const void* fn = (const void*)row2_kernel<T, NPX, V>;
     cudaError_t e = ensure_smem(fn, smem);
     if (e != cudaSuccess) return e;
     RowArgs<T> b = a;
     b.npz = npz;
-    const int grid = persistent_grid(fn, threads, smem, npz);
-    row2_kernel<T, NPX><<<grid, threads, smem, s>>>(b, tw);
+    // persistent over rows: the resident blocks (capped at a.occ per SM when
+    // set) shared among the a.nb tiles of the launch
+    int per_sm = 1, sms = 1;
+    occupancy(fn, threads, smem, &per_sm, &sms);
+    if (a.occ > 0) per_sm = std::min(per_sm, a.occ);
+    const int nb = std::max(1, a.nb);
+    const int gx = std::max(1, std::min(npz, (per_sm * sms + nb - 1) / nb));
+    row2_kernel<T, NPX, V><<<dim3(gx, nb), threads, smem, s>>>(b, tw);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_row(int npx, const RowArgs<T>& a, const cx<T>* tw, int npz, cudaStream_t s) {
+cudaError_t launch_row(int npx, int v, const RowArgs<T>& a, const cx<T>* tw, int npz, cudaStream_t s) {
+    if constexpr (sizeof(T) == 4) {
+        if (v == 1) {
+            switch (npx) {
+            case 768: return launch_row_t<T, 768, 1>(a, tw, npz, s);
+            case 1536: return launch_row_t<T, 1536, 1>(a, tw, npz, s);
+            case 3072: return launch_row_t<T, 3072, 1>(a, tw, npz, s);
+            default: break;
+            }
+        }
+    }
     switch (npx) {
-    case 24: return launch_row_t<T, 24>(a, tw, npz, s);
-    case 48: return launch_row_t<T, 48>(a, tw, npz, s);
-    case 96: return launch_row_t<T, 96>(a, tw, npz, s);
-    case 192: return launch_row_t<T, 192>(a, tw, npz, s);
-    case 384: return launch_row_t<T, 384>(a, tw, npz, s);
-    case 768: return launch_row_t<T, 768>(a, tw, npz, s);
-    case 1536: return launch_row_t<T, 1536>(a, tw, npz, s);
-    case 3072: if constexpr (sizeof(T) == 4) return launch_row_t<T, 3072>(a, tw, npz, s); else return cudaErrorInvalidValue;
+    case 24: return launch_row_t<T, 24, 0>(a, tw, npz, s);
+    case 48: return launch_row_t<T, 48, 0>(a, tw, npz, s);
+    case 96: return launch_row_t<T, 96, 0>(a, tw, npz, s);
+    case 192: return launch_row_t<T, 192, 0>(a, tw, npz, s);
+    case 384: return launch_row_t<T, 384, 0>(a, tw, npz, s);
+    case 768: return launch_row_t<T, 768, 0>(a, tw, npz, s);
+    case 1536: return launch_row_t<T, 1536, 0>(a, tw, npz, s);
+    case 3072: if constexpr (sizeof(T) == 4) return launch_row_t<T, 3072, 0>(a, tw, npz, s); else return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
     }
 }
 
-template <typename T, int NPZ>
+template <typename T, int NPZ, int CB, int V>
 cudaError_t launch_col_t(const ColArgs<T>& a, const cx<T>* tw, cudaStream_t s, int* nblocks) {
-    constexpr int TL = IPlan<NPZ>::TL;
-    constexpr int CB = col_cb<NPZ, (int)sizeof(cx<T>)>();
+    constexpr int TL = IPlan<NPZ, V>::TL;
     constexpr int NZ = 2 * NPZ / 3;
     constexpr int LS = line_stride(NPZ);
     const int threads = CB * TL < 32 ? 32 : CB * TL;
     const int groups = threads / TL;
     const size_t per = (a.kind == COL_FINAL) ? (size_t)col_stride(2 * LS) : (size_t)col_stride(LS + NZ);
     const size_t smem = (size_t)groups * per * sizeof(cx<T>);
+    if (threads > 1024 || smem > (size_t)smem_optin()) return cudaErrorInvalidConfiguration;
     const int grid = (a.hx + CB - 1) / CB;
     if (nblocks) *nblocks = grid;
-    cudaError_t e = ensure_smem((const void*)col2_kernel<T, NPZ, CB>, smem);
+    cudaError_t e = ensure_smem((const void*)col2_kernel<T, NPZ, CB, V>, smem);
     if (e != cudaSuccess) return e;
-    col2_kernel<T, NPZ, CB><<<grid, threads, smem, s>>>(a, tw);
+    col2_kernel<T, NPZ, CB, V><<<dim3(grid, std::max(1, a.nb)), threads, smem, s>>>(a, tw);
     return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t launch_col(int npz, const ColArgs<T>& a, const cx<T>* tw, cudaStream_t s, int* nblocks = nullptr) {
-    switch (npz) {
-    case 24: return launch_col_t<T, 24>(a, tw, s, nblocks);
-    case 48: return launch_col_t<T, 48>(a, tw, s, nblocks);
-    case 96: return launch_col_t<T, 96>(a, tw, s, nblocks);
-    case 192: return launch_col_t<T, 192>(a, tw, s, nblocks);
-    case 384: return launch_col_t<T, 384>(a, tw, s, nblocks);
-    case 768: return launch_col_t<T, 768>(a, tw, s, nblocks);
-    case 1536: return launch_col_t<T, 1536>(a, tw, s, nblocks);
-    case 3072: if constexpr (sizeof(T) == 4) return launch_col_t<T, 3072>(a, tw, s, nblocks); else return cudaErrorInvalidValue;
-    default: return cudaErrorInvalidValue;
+// Columns-per-block choice ci (0 / 1 / 2 = half / default / double) is tuned
+// for FP32 lines of 192 and longer; everything else runs the default.
+template <typename T, int NPZ, int V>
+cudaError_t launch_col_v(int ci, const ColArgs<T>& a, const cx<T>* tw, cudaStream_t s, int* nblocks) {
+    constexpr int ES = (int)sizeof(cx<T>);
+    if constexpr (ES == 8 && NPZ >= 192) {
+        if (ci == 0) return launch_col_t<T, NPZ, col_cb_pick<NPZ, ES, V>(0), V>(a, tw, s, nblocks);
+        if (ci == 2) return launch_col_t<T, NPZ, col_cb_pick<NPZ, ES, V>(2), V>(a, tw, s, nblocks);
     }
+    return launch_col_t<T, NPZ, col_cb<NPZ, ES, V>(), V>(a, tw, s, nblocks);
 }
 
-template <int N> int col_blocks_for(int hx) { return (hx + col_cb<N, 16>() - 1) / col_cb<N, 16>(); }
-// upper bound of column-kernel blocks (the FP64 blocking has the most blocks)
-int col_grid(int npz, int hx) {
+template <typename T>
+cudaError_t launch_col(int npz, int v, int ci, const ColArgs<T>& a, const cx<T>* tw, cudaStream_t s,
+                       int* nblocks = nullptr) {
+    if constexpr (sizeof(T) == 4) {
+        if (v == 1) {
+            switch (npz) {
+            case 768: return launch_col_v<T, 768, 1>(ci, a, tw, s, nblocks);
+            case 1536: return launch_col_v<T, 1536, 1>(ci, a, tw, s, nblocks);
+            case 3072: return launch_col_v<T, 3072, 1>(ci, a, tw, s, nblocks);
+            default: break;
+            }
+        }
+    }
     switch (npz) {
-    case 24: return col_blocks_for<24>(hx); case 48: return col_blocks_for<48>(hx);
-    case 96: return col_blocks_for<96>(hx); case 192: return col_blocks_for<192>(hx);
-    case 384: return col_blocks_for<384>(hx); case 768: return col_blocks_for<768>(hx);
-    case 1536: return col_blocks_for<1536>(hx); case 3072: return col_blocks_for<3072>(hx);
-    default: return 1;
+    case 24: return launch_col_v<T, 24, 0>(ci, a, tw, s, nblocks);
+    case 48: return launch_col_v<T, 48, 0>(ci, a, tw, s, nblocks);
+    case 96: return launch_col_v<T, 96, 0>(ci, a, tw, s, nblocks);
+    case 192: return launch_col_v<T, 192, 0>(ci, a, tw, s, nblocks);
+    case 384: return launch_col_v<T, 384, 0>(ci, a, tw, s, nblocks);
+    case 768: return launch_col_v<T, 768, 0>(ci, a, tw, s, nblocks);
+    case 1536: return launch_col_v<T, 1536, 0>(ci, a, tw, s, nblocks);
+    case 3072: if constexpr (sizeof(T) == 4) return launch_col_v<T, 3072, 0>(ci, a, tw, s, nblocks); else return cudaErrorInvalidValue;
+    default: return cudaErrorInvalidValue;
     }
 }
 
@@ -330,6 +383,10 @@ struct Pipe {
         a.colbase = C(c->col);
         a.fstride = c->fstride;
         a.filter = c->opt.filter;
+        a.tcol = c->tcol;
+        a.tst = c->tst;
+        a.hb = reinterpret_cast<const T*>(c->hb);
+        a.nb = c->nb;
         return a;
     }
 
@@ -346,6 +403,10 @@ struct Pipe {
         a.acc = reinterpret_cast<T*>(c->acc);
         a.s_eta = a.s_etax = a.s_etaz = a.s_psix = a.s_psiz = a.s_g0psi = a.s_F0 = -1;
         for (int l = 0; l < kMaxLines; ++l) { a.fa[l] = -1; a.fb[l] = -1; }
+        a.tcol = c->tcol;
+        a.tacc = c->tacc;
+        a.nb = c->nb;
+        a.occ = c->row_occ;
         return a;
     }
 
@@ -403,7 +464,7 @@ struct Pipe {
             for (int q = 1; q <= M; ++q) out(F.z(0, q), 1, SYM_ZA, q);
             a.nout = o;
             note(c, s, ZK_K_COL_STATE, 2 * Cc + o * U);
-            if ((e = launch_col<T>(c->npz, a, twz, s)) != cudaSuccess) return e;
+            if ((e = launch_col<T>(c->npz, c->plan_v, c->col_ci, a, twz, s)) != cudaSuccess) return e;
             ++nl;
         }
         for (int r = 1; r <= M - 1; ++r) {
@@ -426,7 +487,7 @@ struct Pipe {
                 const double wr = U + (r >= 2 ? Pp : 0.0);
                 note(c, s, ZK_K_ROW_ROUND, rd + wr);
             }
-            if ((e = launch_row<T>(c->npx, ra, twx, c->npz, s)) != cudaSuccess) return e;
+            if ((e = launch_row<T>(c->npx, c->plan_v, ra, twx, c->npz, s)) != cudaSuccess) return e;
             ++nl;
             ColArgs<T> a = col_base(c);
             a.kind = COL_PHI;
@@ -437,7 +498,7 @@ struct Pipe {
             }
             a.nout = o;
             note(c, s, ZK_K_COL_PHI, (1 + o) * U);
-            if ((e = launch_col<T>(c->npz, a, twz, s)) != cudaSuccess) return e;
+            if ((e = launch_col<T>(c->npz, c->plan_v, c->col_ci, a, twz, s)) != cudaSuccess) return e;
             ++nl;
         }
         {
@@ -459,7 +520,7 @@ struct Pipe {
             ra.out0 = C(c->col) + (long long)F.gnl() * c->fstride;
             ra.out1 = C(c->col) + (long long)F.npsi() * c->fstride;
             note(c, s, ZK_K_ROW_FINAL, (5 + (M >= 2 ? M : 0) + 2) * U + (M >= 3 ? Pp : 0.0));
-            if ((e = launch_row<T>(c->npx, ra, twx, c->npz, s)) != cudaSuccess) return e;
+            if ((e = launch_row<T>(c->npx, c->plan_v, ra, twx, c->npz, s)) != cudaSuccess) return e;
             ++nl;
         }
         {
@@ -480,7 +541,7 @@ struct Pipe {
                 }
                 note(c, s, ZK_K_COL_FINAL, b);
             }
-            if ((e = launch_col<T>(c->npz, fin, twz, s, &c->fin_blocks)) != cudaSuccess) return e;
+            if ((e = launch_col<T>(c->npz, c->plan_v, c->col_ci, fin, twz, s, &c->fin_blocks)) != cudaSuccess) return e;
             ++nl;
         }
         if (nlaunch) *nlaunch += nl;
@@ -592,8 +653,8 @@ struct Pipe {
 // Stockham tables (length-n w_n^t) for the unpadded state transforms; per-stage
 // tables of the in-place plans for the padded right-hand-side transforms.
 template <typename T>
-void make_plan_twiddles(int n, std::vector<cx<T>>& out) {
-    const PlanDesc d = plan_desc_of(n);
+void make_plan_twiddles(int n, int v, std::vector<cx<T>>& out) {
+    const PlanDesc d = plan_desc_of(n, v);
     const int ne = plan_table_size(d);
     out.resize(ne);
     for (int e = 0; e < ne; ++e) {
@@ -606,21 +667,33 @@ void make_plan_twiddles(int n, std::vector<cx<T>>& out) {
 }
 
 template <typename T>
-zk_status alloc_twiddles(zk_ctx* c) {
-    int ns[4] = {c->nx, c->nz, c->npx, c->npz};
-    void** dst[4] = {&c->tw_x, &c->tw_z, &c->tw_px, &c->tw_pz};
-    for (int i = 0; i < 4; ++i) {
-        std::vector<cx<T>> h;
-        if (i < 2) make_twiddles<T>(ns[i], h);
-        else make_plan_twiddles<T>(ns[i], h);
-        void* p = nullptr;
-        if (cudaMalloc(&p, h.size() * sizeof(cx<T>)) != cudaSuccess) return ZK_ENOMEM;
-        c->allocs.push_back(p);
-        c->bytes += h.size() * sizeof(cx<T>);
-        if (cudaMemcpy(p, h.data(), h.size() * sizeof(cx<T>), cudaMemcpyHostToDevice) != cudaSuccess) return ZK_ECUDA;
-        *dst[i] = p;
-    }
+zk_status upload(zk_ctx* c, const std::vector<cx<T>>& h, void** dst) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, h.size() * sizeof(cx<T>)) != cudaSuccess) { cudaGetLastError(); return ZK_ENOMEM; }
+    c->allocs.push_back(p);
+    c->bytes += h.size() * sizeof(cx<T>);
+    if (cudaMemcpy(p, h.data(), h.size() * sizeof(cx<T>), cudaMemcpyHostToDevice) != cudaSuccess) return ZK_ECUDA;
+    *dst = p;
     return ZK_OK;
+}
+
+template <typename T>
+zk_status alloc_twiddles(zk_ctx* c) {
+    std::vector<cx<T>> h;
+    make_twiddles<T>(c->nx, h);
+    zk_status st = upload<T>(c, h, &c->tw_x);
+    if (st == ZK_OK) { make_twiddles<T>(c->nz, h); st = upload<T>(c, h, &c->tw_z); }
+    const int np[2] = {c->npx, c->npz};
+    for (int v = 0; v < 2 && st == ZK_OK; ++v) {
+        for (int i = 0; i < 2 && st == ZK_OK; ++i) {
+            if (v == 1 && !plan_has_variant(np[i])) { c->tw_pv[1][i] = c->tw_pv[0][i]; continue; }
+            make_plan_twiddles<T>(np[i], v, h);
+            st = upload<T>(c, h, &c->tw_pv[v][i]);
+        }
+    }
+    c->tw_px = c->tw_pv[0][0];
+    c->tw_pz = c->tw_pv[0][1];
+    return st;
 }
 
 zk_status dalloc(zk_ctx* c, void** p, size_t bytes) {
@@ -730,41 +803,97 @@ void zk_destroy(zk_ctx* c) {
     delete c;
 }
 
-zk_status zk_create(zk_ctx** out, int nx, int nz, double Lx, double Lz, double h, double g, int M, int precision) {
-    if (!out) return ZK_EINVAL;
+}  // extern "C"
+
+namespace {
+
+// One context over nb tiles of the same grid and order with depths h[0..nb-1].
+zk_status ctx_create(zk_ctx** out, int nx, int nz, double Lx, double Lz, const double* h, int nb, double g, int M,
+                     int precision) {
+    if (!out || !h || nb < 1) return ZK_EINVAL;
     *out = nullptr;
     if (!is_pow2(nx) || !is_pow2(nz) || nx < 16 || nz < 16) return ZK_EINVAL;
     const int nmax = precision == ZK_F64 ? 1024 : 2048;
     if (nx > nmax || nz > nmax) return ZK_EINVAL;
-    if (!(Lx > 0) || !(Lz > 0) || !(h > 0) || !(g > 0)) return ZK_EINVAL;
+    if (!(Lx > 0) || !(Lz > 0) || !(g > 0)) return ZK_EINVAL;
+    for (int t = 0; t < nb; ++t) if (!(h[t] > 0)) return ZK_EINVAL;
     if (M < 1 || M > ZK_MAX_ORDER) return ZK_EINVAL;
     if (precision != ZK_F32 && precision != ZK_F64) return ZK_EINVAL;
     zk_ctx* c = new (std::nothrow) zk_ctx();
     if (!c) return ZK_ENOMEM;
     c->nx = nx; c->nz = nz; c->npx = 3 * nx / 2; c->npz = 3 * nz / 2; c->hx = nx / 2;
-    c->Lx = Lx; c->Lz = Lz; c->h = h; c->g = g; c->M = M; c->prec = precision;
+    c->Lx = Lx; c->Lz = Lz; c->h = h[0]; c->g = g; c->M = M; c->prec = precision;
     c->opt.eps = 1.0; c->opt.integrator = ZK_RK4; c->opt.taper = 1; c->opt.filter = 1; c->opt.stream = nullptr;
+    c->nb = nb;
+    c->hv.assign(h, h + nb);
     cudaGetDevice(&c->device);
     c->csz = precision == ZK_F32 ? 8 : 16;
     const size_t rsz = precision == ZK_F32 ? 4 : 8;
     zk_status st = precision == ZK_F32 ? alloc_twiddles<float>(c) : alloc_twiddles<double>(c);
-    const size_t compact = (size_t)nz * c->hx * c->csz;
+    c->tst = (long long)nz * c->hx;
+    const size_t compact = (size_t)c->tst * c->csz * nb;
     void** comp[10] = {&c->y_eta, &c->y_psi, &c->ys_eta, &c->ys_psi, &c->ka_eta, &c->ka_psi,
                        &c->ko_eta, &c->ko_psi, &c->h_eta, &c->h_psi};
     for (int i = 0; i < 10 && st == ZK_OK; ++i) st = dalloc(c, comp[i], compact);
     const Fields F{M};
     c->nfields = F.count();
     c->fstride = (long long)c->npz * c->hx;
-    if (st == ZK_OK) st = dalloc(c, &c->col, (size_t)c->nfields * c->fstride * c->csz);
-    if (st == ZK_OK) st = dalloc(c, &c->acc, (size_t)c->npz * c->npx * rsz);
+    c->tcol = (long long)c->nfields * c->fstride;
+    c->tacc = (long long)c->npz * c->npx;
+    if (st == ZK_OK) st = dalloc(c, &c->col, (size_t)c->tcol * c->csz * nb);
+    if (st == ZK_OK) st = dalloc(c, &c->acc, (size_t)c->tacc * rsz * nb);
     if (st == ZK_OK) st = dalloc(c, &c->stage, (size_t)2 * nx * nz * kIoElem);
     if (st == ZK_OK) st = dalloc(c, &c->tank, (size_t)2 * (nx / 2) * (nz / 2) * 8);
-    c->npartial = col_grid(c->npz, c->hx);
+    c->npartial = c->hx * nb;              // at most one column-kernel block per column
     if (st == ZK_OK) st = dalloc(c, (void**)&c->partial, (size_t)3 * c->npartial * sizeof(double));
     if (st == ZK_OK) st = dalloc(c, (void**)&c->esum, 4 * sizeof(double));
+    if (st == ZK_OK && nb > 1) {
+        st = dalloc(c, &c->hb, (size_t)nb * rsz);
+        if (st == ZK_OK) {
+            std::vector<float> hf(h, h + nb);
+            const void* src = precision == ZK_F32 ? (const void*)hf.data() : (const void*)h;
+            if (cudaMemcpy(c->hb, src, (size_t)nb * rsz, cudaMemcpyHostToDevice) != cudaSuccess) st = ZK_ECUDA;
+        }
+    }
     if (st != ZK_OK) { zk_destroy(c); return st; }
     *out = c;
     return ZK_OK;
+}
+
+// Single-tile view of tile t of a group context: the same buffers offset to the
+// tile, depth h[t]; owns nothing (never destroyed), has no graph.
+void tile_view(const zk_ctx* g, int t, zk_ctx* v) {
+    v->nx = g->nx; v->nz = g->nz; v->npx = g->npx; v->npz = g->npz; v->hx = g->hx; v->M = g->M; v->prec = g->prec;
+    v->Lx = g->Lx; v->Lz = g->Lz; v->h = g->hv[t]; v->g = g->g;
+    v->opt = g->opt;
+    v->device = g->device;
+    v->has_state = true;
+    v->csz = g->csz;
+    v->tw_x = g->tw_x; v->tw_z = g->tw_z; v->tw_px = g->tw_px; v->tw_pz = g->tw_pz;
+    const size_t oc = (size_t)t * g->tst * g->csz;
+    auto off = [&](void* p, size_t o) { return p ? (void*)((char*)p + o) : nullptr; };
+    v->y_eta = off(g->y_eta, oc); v->y_psi = off(g->y_psi, oc);
+    v->ys_eta = off(g->ys_eta, oc); v->ys_psi = off(g->ys_psi, oc);
+    v->ka_eta = off(g->ka_eta, oc); v->ka_psi = off(g->ka_psi, oc);
+    v->ko_eta = off(g->ko_eta, oc); v->ko_psi = off(g->ko_psi, oc);
+    v->h_eta = off(g->h_eta, oc); v->h_psi = off(g->h_psi, oc);
+    v->col = off(g->col, (size_t)t * g->tcol * g->csz);
+    v->acc = off(g->acc, (size_t)t * g->tacc * (g->prec == ZK_F32 ? 4 : 8));
+    v->nfields = g->nfields;
+    v->fstride = g->fstride;
+    v->stage = g->stage; v->tank = g->tank;
+    v->partial = g->partial; v->npartial = g->npartial; v->esum = g->esum;
+    v->nb = 1; v->tcol = 0; v->tst = 0; v->tacc = 0; v->hb = nullptr;
+    v->hv.assign(1, g->hv[t]);
+    v->plan_v = g->plan_v; v->col_ci = g->col_ci; v->row_occ = g->row_occ;
+}
+
+}  // namespace
+
+extern "C" {
+
+zk_status zk_create(zk_ctx** out, int nx, int nz, double Lx, double Lz, double h, double g, int M, int precision) {
+    return ctx_create(out, nx, nz, Lx, Lz, &h, 1, g, M, precision);
 }
 
 zk_status zk_set_options(zk_ctx* c, const zk_options* o) {
@@ -1062,6 +1191,378 @@ zk_status zk_launches_per_step(const zk_ctx* c, int* n) {
     if (!c || !n) return ZK_EINVAL;
     *n = (c->opt.integrator == ZK_IFAB2 ? 1 : 4) * (2 * c->M + 1);
     return ZK_OK;
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// Batched tiles: groups of tiles that share grid and order, one launch per
+// pass of a group (blockIdx.y = tile), the groups as parallel branches of one
+// captured step graph.
+// ===========================================================================
+struct zk_batch {
+    int ntiles = 0, prec = ZK_F32;
+    std::vector<zk_ctx*> groups;
+    std::vector<std::pair<int, int>> where;    // tile -> (group, index in group)
+    std::vector<char> has_state;
+    std::vector<cudaStream_t> gs;              // one capture branch per group
+    std::vector<cudaEvent_t> join;
+    cudaEvent_t fork = nullptr;
+    cudaStream_t cap = nullptr;
+    zk_options opt{};
+    cudaGraphExec_t gexec = nullptr, gexec_boot = nullptr;
+    bool gvalid = false;
+    double gdt = 0.0;
+    bool ab_valid = false;
+    double ab_dt = 0.0;
+    int launches_per_step = 0;
+};
+
+namespace {
+
+void batch_drop_graph(zk_batch* b) {
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->gexec_boot) cudaGraphExecDestroy(b->gexec_boot);
+    b->gexec = b->gexec_boot = nullptr;
+    b->gvalid = false;
+}
+
+zk_status batch_capture(zk_batch* b, double dt, int variant, cudaGraphExec_t* out, int* nl) {
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed) != cudaSuccess) return ZK_ECUDA;
+    cudaError_t e = cudaEventRecord(b->fork, b->cap);
+    // every forked branch is joined back, also after a failed enqueue, so
+    // that the capture ends with no stream left capturing
+    for (size_t i = 0; i < b->groups.size() && e == cudaSuccess; ++i) {
+        e = cudaStreamWaitEvent(b->gs[i], b->fork, 0);
+        if (e != cudaSuccess) break;
+        const cudaError_t eq = enqueue_step_any(b->groups[i], dt, b->gs[i], nl, variant);
+        e = cudaEventRecord(b->join[i], b->gs[i]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->cap, b->join[i], 0);
+        if (e == cudaSuccess) e = eq;
+    }
+    cudaError_t e2 = cudaStreamEndCapture(b->cap, &graph);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return ZK_ECUDA;
+    }
+    e = cudaGraphInstantiate(out, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) { *out = nullptr; return ZK_ECUDA; }
+    return ZK_OK;
+}
+
+zk_status batch_build_graph(zk_batch* b, double dt) {
+    batch_drop_graph(b);
+    int nl = 0;
+    zk_status st;
+    if (b->opt.integrator == ZK_IFAB2) {
+        st = batch_capture(b, dt, 1, &b->gexec_boot, &nl);
+        nl = 0;
+        if (st == ZK_OK) st = batch_capture(b, dt, 2, &b->gexec, &nl);
+    } else {
+        st = batch_capture(b, dt, 0, &b->gexec, &nl);
+    }
+    if (st != ZK_OK) { batch_drop_graph(b); return st; }
+    b->gvalid = true;
+    b->gdt = dt;
+    b->launches_per_step = nl;
+    return ZK_OK;
+}
+
+// Tuning cache: a JSON object {"entries": {"<key>": {"plan_v": v, "col_ci": c,
+// "row_occ": o, "ms": t}, ...}} with one entry per line; the key names the
+// device, grid, order, precision and tile count.
+std::string tune_key(const zk_ctx* c) {
+    cudaDeviceProp pr;
+    std::string dev = "gpu";
+    if (cudaGetDeviceProperties(&pr, c->device) == cudaSuccess) dev = pr.name;
+    for (char& ch : dev) if (ch == '"' || ch == '\\') ch = '_';
+    char k[256];
+    snprintf(k, sizeof(k), "%s/%dx%d/M%d/%s/nb%d", dev.c_str(), c->nx, c->nz, c->M, c->prec == ZK_F32 ? "f32" : "f64", c->nb);
+    return k;
+}
+
+struct TuneEntry { int plan_v, col_ci, row_occ; double ms; };
+
+std::vector<std::pair<std::string, TuneEntry>> tune_load(const char* path) {
+    std::vector<std::pair<std::string, TuneEntry>> out;
+    if (!path) return out;
+    FILE* f = fopen(path, "r");
+    if (!f) return out;
+    char line[1024];
+    while (fgets(line, sizeof(line), f)) {
+        const char* q0 = strchr(line, '"');
+        if (!q0) continue;
+        const char* q1 = strchr(q0 + 1, '"');
+        if (!q1) continue;
+        const char* body = strstr(q1, "\"plan_v\"");
+        if (!body) continue;
+        TuneEntry t{};
+        if (sscanf(body, "\"plan_v\": %d, \"col_ci\": %d, \"row_occ\": %d, \"ms\": %lf", &t.plan_v, &t.col_ci,
+                   &t.row_occ, &t.ms) == 4 &&
+            t.plan_v >= 0 && t.plan_v <= 1 && t.col_ci >= 0 && t.col_ci <= 2 && t.row_occ >= 0 && t.row_occ <= 64)
+            out.push_back({std::string(q0 + 1, q1), t});
+    }
+    fclose(f);
+    return out;
+}
+
+bool tune_save(const char* path, const std::vector<std::pair<std::string, TuneEntry>>& es) {
+    if (!path) return true;
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE* f = fopen(tmp.c_str(), "w");
+    if (!f) return false;
+    fprintf(f, "{\"version\": 1, \"entries\": {\n");
+    for (size_t i = 0; i < es.size(); ++i)
+        fprintf(f, "\"%s\": {\"plan_v\": %d, \"col_ci\": %d, \"row_occ\": %d, \"ms\": %.6f}%s\n", es[i].first.c_str(),
+                es[i].second.plan_v, es[i].second.col_ci, es[i].second.row_occ, es[i].second.ms,
+                i + 1 < es.size() ? "," : "");
+    fprintf(f, "}}\n");
+    const bool ok = fclose(f) == 0;
+    return ok && rename(tmp.c_str(), path) == 0;
+}
+
+// Mean ms of one eager step of group c under the launch shape (v, ci, occ), or
+// a negative value when the shape cannot launch (threads or shared memory).
+double time_shape(zk_ctx* c, double dt, int v, int ci, int occ, cudaStream_t s, int reps) {
+    c->plan_v = v; c->col_ci = ci; c->row_occ = occ;
+    c->tw_px = c->tw_pv[v][0];
+    c->tw_pz = c->tw_pv[v][1];
+    const int variant = c->opt.integrator == ZK_IFAB2 ? 1 : 0;
+    if (enqueue_step_any(c, dt, s, nullptr, variant) != cudaSuccess) { cudaStreamSynchronize(s); cudaGetLastError(); return -1.0; }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, s);
+    cudaError_t e = cudaSuccess;
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) e = enqueue_step_any(c, dt, s, nullptr, variant);
+    cudaEventRecord(e1, s);
+    cudaError_t es = cudaStreamSynchronize(s);
+    float ms = -1.f;
+    if (e == cudaSuccess && es == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaGetLastError();
+    return (e == cudaSuccess && es == cudaSuccess) ? ms / reps : -1.0;
+}
+
+}  // namespace
+
+extern "C" {
+
+void zk_batch_destroy(zk_batch* b) {
+    if (!b) return;
+    batch_drop_graph(b);
+    for (zk_ctx* c : b->groups) zk_destroy(c);
+    for (cudaStream_t s : b->gs) cudaStreamDestroy(s);
+    for (cudaEvent_t e : b->join) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    delete b;
+}
+
+zk_status zk_batch_create(zk_batch** out, int ntiles, const int* nx, const int* nz, const double* Lx,
+                          const double* Lz, const double* h, double g, const int* M, int precision) {
+    if (!out || ntiles < 1 || !nx || !nz || !Lx || !Lz || !h || !M) return ZK_EINVAL;
+    *out = nullptr;
+    zk_batch* b = new (std::nothrow) zk_batch();
+    if (!b) return ZK_ENOMEM;
+    b->ntiles = ntiles;
+    b->prec = precision;
+    b->where.resize(ntiles);
+    b->has_state.assign(ntiles, 0);
+    // group tiles by (nx, nz, Lx, Lz, M) in order of first appearance
+    std::vector<std::vector<int>> members;
+    for (int t = 0; t < ntiles; ++t) {
+        int gi = -1;
+        for (size_t k = 0; k < members.size(); ++k) {
+            const int r = members[k][0];
+            if (nx[r] == nx[t] && nz[r] == nz[t] && Lx[r] == Lx[t] && Lz[r] == Lz[t] && M[r] == M[t]) { gi = (int)k; break; }
+        }
+        if (gi < 0) { gi = (int)members.size(); members.emplace_back(); }
+        b->where[t] = {gi, (int)members[gi].size()};
+        members[gi].push_back(t);
+    }
+    zk_status st = ZK_OK;
+    for (size_t k = 0; k < members.size() && st == ZK_OK; ++k) {
+        const int r = members[k][0];
+        std::vector<double> hs;
+        for (int t : members[k]) hs.push_back(h[t]);
+        zk_ctx* c = nullptr;
+        st = ctx_create(&c, nx[r], nz[r], Lx[r], Lz[r], hs.data(), (int)hs.size(), g, M[r], precision);
+        if (st == ZK_OK) {
+            b->groups.push_back(c);
+            cudaStream_t s = nullptr;
+            cudaEvent_t e = nullptr;
+            if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) st = ZK_ECUDA;
+            else b->gs.push_back(s);
+            if (st == ZK_OK && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) st = ZK_ECUDA;
+            else if (st == ZK_OK) b->join.push_back(e);
+        }
+    }
+    if (st == ZK_OK && cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) st = ZK_ECUDA;
+    if (st == ZK_OK && cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) st = ZK_ECUDA;
+    b->opt.eps = 1.0; b->opt.integrator = ZK_RK4; b->opt.taper = 1; b->opt.filter = 1; b->opt.stream = nullptr;
+    if (st != ZK_OK) { zk_batch_destroy(b); return st; }
+    *out = b;
+    return ZK_OK;
+}
+
+zk_status zk_batch_set_options(zk_batch* b, const zk_options* o) {
+    if (!b || !o) return ZK_EINVAL;
+    for (zk_ctx* c : b->groups) {
+        zk_status st = zk_set_options(c, o);
+        if (st != ZK_OK) return st;
+    }
+    if (o->integrator != b->opt.integrator || o->eps != b->opt.eps || o->taper != b->opt.taper) b->ab_valid = false;
+    b->opt = *o;
+    batch_drop_graph(b);
+    return ZK_OK;
+}
+
+zk_status zk_batch_set_state(zk_batch* b, int tile, const void* eta, const void* psi, int dtype, int on_device) {
+    if (!b || tile < 0 || tile >= b->ntiles) return ZK_EINVAL;
+    zk_ctx v;
+    tile_view(b->groups[b->where[tile].first], b->where[tile].second, &v);
+    zk_status st = zk_set_state(&v, eta, psi, dtype, on_device);
+    if (st == ZK_OK) { b->has_state[tile] = 1; b->ab_valid = false; }
+    return st;
+}
+
+zk_status zk_batch_get_state(zk_batch* b, int tile, void* eta, void* psi, int dtype, int on_device) {
+    if (!b || tile < 0 || tile >= b->ntiles) return ZK_EINVAL;
+    if (!b->has_state[tile]) return ZK_ESTATE;
+    zk_ctx v;
+    tile_view(b->groups[b->where[tile].first], b->where[tile].second, &v);
+    return zk_get_state(&v, eta, psi, dtype, on_device);
+}
+
+zk_status zk_batch_energy(zk_batch* b, int tile, double* H, double* kin, double* pot, double* mean_eta) {
+    if (!b || tile < 0 || tile >= b->ntiles) return ZK_EINVAL;
+    if (!b->has_state[tile]) return ZK_ESTATE;
+    zk_ctx v;
+    tile_view(b->groups[b->where[tile].first], b->where[tile].second, &v);
+    return zk_energy(&v, H, kin, pot, mean_eta);
+}
+
+zk_status zk_batch_step(zk_batch* b, double dt, int n) {
+    if (!b || n < 0 || !(dt > 0) || !std::isfinite(dt)) return ZK_EINVAL;
+    for (int t = 0; t < b->ntiles; ++t) if (!b->has_state[t]) return ZK_ESTATE;
+    if (n == 0) return ZK_OK;
+    if (!b->gvalid || b->gdt != dt) {
+        zk_status st = batch_build_graph(b, dt);
+        if (st != ZK_OK) return st;
+    }
+    cudaStream_t s = (cudaStream_t)b->opt.stream;
+    for (int i = 0; i < n; ++i) {
+        cudaGraphExec_t g = b->gexec;
+        if (b->opt.integrator == ZK_IFAB2 && !(b->ab_valid && b->ab_dt == dt)) {
+            g = b->gexec_boot;
+            b->ab_valid = true;
+            b->ab_dt = dt;
+        }
+        if (cudaGraphLaunch(g, s) != cudaSuccess) return ZK_ECUDA;
+    }
+    return ZK_OK;
+}
+
+zk_status zk_batch_sync(zk_batch* b) {
+    if (!b) return ZK_EINVAL;
+    return cu(cudaStreamSynchronize((cudaStream_t)b->opt.stream));
+}
+
+zk_status zk_batch_info(const zk_batch* b, int* ngroups, int* launches_per_step, size_t* device_bytes) {
+    if (!b) return ZK_EINVAL;
+    if (ngroups) *ngroups = (int)b->groups.size();
+    if (launches_per_step) {
+        int n = 0;
+        for (const zk_ctx* c : b->groups) n += (b->opt.integrator == ZK_IFAB2 ? 1 : 4) * (2 * c->M + 1);
+        *launches_per_step = n;
+    }
+    if (device_bytes) {
+        size_t by = 0;
+        for (const zk_ctx* c : b->groups) by += c->bytes;
+        *device_bytes = by;
+    }
+    return ZK_OK;
+}
+
+zk_status zk_batch_group(const zk_batch* b, int gi, int* nx, int* nz, int* M, int* ntiles, int* plan_v, int* col_ci,
+                         int* row_occ) {
+    if (!b || gi < 0 || gi >= (int)b->groups.size()) return ZK_EINVAL;
+    const zk_ctx* c = b->groups[gi];
+    if (nx) *nx = c->nx;
+    if (nz) *nz = c->nz;
+    if (M) *M = c->M;
+    if (ntiles) *ntiles = c->nb;
+    if (plan_v) *plan_v = c->plan_v;
+    if (col_ci) *col_ci = c->col_ci;
+    if (row_occ) *row_occ = c->row_occ;
+    return ZK_OK;
+}
+
+zk_status zk_batch_set_shape(zk_batch* b, int gi, int plan_v, int col_ci, int row_occ) {
+    if (!b || gi < 0 || gi >= (int)b->groups.size()) return ZK_EINVAL;
+    if (plan_v < 0 || plan_v > 1 || col_ci < 0 || col_ci > 2 || row_occ < 0 || row_occ > 64) return ZK_EINVAL;
+    zk_ctx* c = b->groups[gi];
+    c->plan_v = plan_v; c->col_ci = col_ci; c->row_occ = row_occ;
+    c->tw_px = c->tw_pv[plan_v][0];
+    c->tw_pz = c->tw_pv[plan_v][1];
+    batch_drop_graph(b);
+    return ZK_OK;
+}
+
+zk_status zk_batch_autotune(zk_batch* b, double dt, const char* cache_path, int* tuned, int* cached) {
+    if (!b || !(dt > 0) || !std::isfinite(dt)) return ZK_EINVAL;
+    for (int t = 0; t < b->ntiles; ++t) if (!b->has_state[t]) return ZK_ESTATE;
+    if (cudaStreamSynchronize((cudaStream_t)b->opt.stream) != cudaSuccess) return ZK_ECUDA;   // states set
+    auto cache = tune_load(cache_path);
+    int nt = 0, nc = 0;
+    bool dirty = false;
+    zk_status st = ZK_OK;
+    for (size_t gi = 0; gi < b->groups.size() && st == ZK_OK; ++gi) {
+        zk_ctx* c = b->groups[gi];
+        const std::string key = tune_key(c);
+        const TuneEntry* hit = nullptr;
+        for (auto& kv : cache) if (kv.first == key) hit = &kv.second;
+        if (hit) {
+            zk_batch_set_shape(b, (int)gi, hit->plan_v, hit->col_ci, hit->row_occ);
+            ++nc;
+            continue;
+        }
+        // the timing steps advance the group: keep its state and forcing history
+        cudaStream_t s = b->gs[gi];
+        const size_t bytes = (size_t)c->tst * c->csz * c->nb;
+        void* save = nullptr;
+        if (cudaMalloc(&save, 4 * bytes) != cudaSuccess) { cudaGetLastError(); return ZK_ENOMEM; }
+        void* src[4] = {c->y_eta, c->y_psi, c->h_eta, c->h_psi};
+        for (int i = 0; i < 4; ++i) cudaMemcpyAsync((char*)save + i * bytes, src[i], bytes, cudaMemcpyDeviceToDevice, s);
+        const bool var = plan_has_variant(c->npx) || plan_has_variant(c->npz);
+        TuneEntry best{0, 1, 0, -1.0};
+        for (int v = 0; v <= (var && c->prec == ZK_F32 ? 1 : 0); ++v)
+            for (int ci = 0; ci <= 2; ++ci)
+                for (int occ : {0, 1, 2}) {
+                    if (c->prec != ZK_F32 && ci != 1) continue;
+                    const double ms = time_shape(c, dt, v, ci, occ, s, 3);
+                    if (ms > 0 && (best.ms < 0 || ms < best.ms)) best = {v, ci, occ, ms};
+                }
+        for (int i = 0; i < 4; ++i) cudaMemcpyAsync(src[i], (char*)save + i * bytes, bytes, cudaMemcpyDeviceToDevice, s);
+        cudaError_t e = cudaStreamSynchronize(s);
+        cudaFree(save);
+        if (e != cudaSuccess) return ZK_ECUDA;
+        if (best.ms < 0) { best = {0, 1, 0, 0.0}; st = ZK_ECUDA; }
+        zk_batch_set_shape(b, (int)gi, best.plan_v, best.col_ci, best.row_occ);
+        cache.push_back({key, best});
+        dirty = true;
+        ++nt;
+    }
+    b->ab_valid = false;   // the timing steps used the history buffers
+    if (dirty && !tune_save(cache_path, cache) && st == ZK_OK) st = ZK_EINVAL;
+    if (tuned) *tuned = nt;
+    if (cached) *cached = nc;
+    return st;
 }
 
 }  // extern "C"

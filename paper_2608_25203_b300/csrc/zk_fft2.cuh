@@ -220,9 +220,14 @@ __device__ __forceinline__ void dit_last_blk(const cx<T>* buf, const cx<T>* __re
 // DIF order. The last DIF stage is radix 16 (or 8 for the smallest line):
 // its stride-16 groups land on distinct banks with the pad-per-16 layout,
 // and TL divides N/R for every radix.
-template <int N> struct IPlan;
-#define ZK_IPLAN(N_, TL_, R1_, ...)                                                                      \
-    template <> struct IPlan<N_> {                                                                       \
+//
+// Variant V = 0 is the default plan of each length. V = 1 is an alternative
+// for the long lines (radix 16 throughout, half the line-group width of the
+// radix-8 plan at the same shared memory per line); for the short lines it is
+// the default plan again. The batch autotuner times both per tile shape.
+template <int N, int V = 0> struct IPlan;
+#define ZK_IPLAN(N_, V_, TL_, R1_, ...)                                                                  \
+    template <> struct IPlan<N_, V_> {                                                                   \
         static constexpr int TL = TL_, R1 = R1_;                                                         \
         static constexpr int RADICES[] = {R1_, __VA_ARGS__};                                             \
         static constexpr int NSTAGE = sizeof(RADICES) / sizeof(int);                                     \
@@ -246,35 +251,42 @@ template <int N> struct IPlan;
             dit_last_blk<N_, R1_, INV, T>(b, tws, tid, nt, st);                                          \
         }                                                                                                \
     };
-ZK_IPLAN(24, 1, 3, 8)
-ZK_IPLAN(48, 1, 3, 16)
-ZK_IPLAN(96, 2, 6, 16)
-ZK_IPLAN(192, 4, 12, 16)
-ZK_IPLAN(384, 8, 6, 4, 16)
-#ifdef ZK_RADIX16_PLANS
-ZK_IPLAN(768, 16, 3, 16, 16)
-ZK_IPLAN(1536, 32, 6, 16, 16)
-ZK_IPLAN(3072, 64, 12, 16, 16)
-#else
+ZK_IPLAN(24, 0, 1, 3, 8)
+ZK_IPLAN(48, 0, 1, 3, 16)
+ZK_IPLAN(96, 0, 2, 6, 16)
+ZK_IPLAN(192, 0, 4, 12, 16)
+ZK_IPLAN(384, 0, 8, 6, 4, 16)
 // radix-8 plans: every stage has N/R divisible by 128 (3072), 64 (1536) or
-// 32 (768), twice the line-group width of the radix-16 plans at the same
-// shared memory per line; one 2-way bank conflict remains in the third stage
-ZK_IPLAN(768, 32, 3, 4, 8, 8)
-ZK_IPLAN(1536, 64, 3, 8, 8, 8)
-ZK_IPLAN(3072, 128, 6, 8, 8, 8)
-#endif
+// 32 (768); one 2-way bank conflict remains in the third stage
+ZK_IPLAN(768, 0, 32, 3, 4, 8, 8)
+ZK_IPLAN(1536, 0, 64, 3, 8, 8, 8)
+ZK_IPLAN(3072, 0, 128, 6, 8, 8, 8)
+ZK_IPLAN(768, 1, 16, 3, 16, 16)
+ZK_IPLAN(1536, 1, 32, 6, 16, 16)
+ZK_IPLAN(3072, 1, 64, 12, 16, 16)
 #undef ZK_IPLAN
+template <int N> struct IPlan<N, 1> : IPlan<N, 0> {};
+// lengths whose V = 1 plan differs from the default
+__host__ __device__ constexpr bool plan_has_variant(int n) { return n == 768 || n == 1536 || n == 3072; }
 
 // Host/device description of a plan for building its twiddle table.
 struct PlanDesc {
     int n, nstage, radix[4];
 };
-template <int N> __host__ __device__ constexpr PlanDesc plan_desc() {
-    PlanDesc d{N, IPlan<N>::NSTAGE, {1, 1, 1, 1}};
-    for (int i = 0; i < IPlan<N>::NSTAGE; ++i) d.radix[i] = IPlan<N>::RADICES[i];
+template <int N, int V = 0> __host__ __device__ constexpr PlanDesc plan_desc() {
+    PlanDesc d{N, IPlan<N, V>::NSTAGE, {1, 1, 1, 1}};
+    for (int i = 0; i < IPlan<N, V>::NSTAGE; ++i) d.radix[i] = IPlan<N, V>::RADICES[i];
     return d;
 }
-inline PlanDesc plan_desc_of(int n) {
+inline PlanDesc plan_desc_of(int n, int v = 0) {
+    if (v == 1 && plan_has_variant(n)) {
+        switch (n) {
+        case 768: return plan_desc<768, 1>();
+        case 1536: return plan_desc<1536, 1>();
+        case 3072: return plan_desc<3072, 1>();
+        default: break;
+        }
+    }
     switch (n) {
     case 24: return plan_desc<24>();
     case 48: return plan_desc<48>();

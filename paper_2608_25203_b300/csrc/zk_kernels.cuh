@@ -73,6 +73,11 @@ struct RowArgs {
     cx<T>* out0;             // column-space output (Phi(r), or G_nl)
     cx<T>* out1;             // N_psi (final round)
     int npz;                 // padded rows (persistent row kernels loop over them)
+    // batched tiles (blockIdx.y = tile): element offsets of one tile's
+    // column-space fields and of its accumulator; 0 for a single grid
+    long long tcol, tacc;
+    int nb;                  // tiles in the launch (host side: grid.y)
+    int occ;                 // host side: resident blocks per SM to use (0 = all)
 };
 
 // ---------------------------------------------------------------------------
@@ -114,6 +119,11 @@ struct ColArgs {
     cx<T>* h_eta; cx<T>* h_psi;     // IF-AB2: nonlinear forcing of the previous step
     const cx<T>* v_hat;             // inverse DNO: target v = G(eta) psi (compact)
     int ab_first;                   // IF-AB2: 1 = bootstrap with IF-Euler (F* = F_n)
+    // batched tiles (blockIdx.y = tile): element offsets of one tile's
+    // column-space fields and of its compact spectra, per-tile depth h
+    long long tcol, tst;
+    const T* hb;                    // nullptr: every tile has depth h
+    int nb;                         // tiles in the launch (host side: grid.y)
 };
 
 static __global__ void energy_finalize_kernel(const double* __restrict__ partial, int n, double* __restrict__ out) {

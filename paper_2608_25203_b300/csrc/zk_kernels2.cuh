@@ -24,9 +24,9 @@ template <> __device__ __forceinline__ void d_sincos<double>(double x, double* s
 // ---------------------------------------------------------------------------
 // Row kernel: persistent over padded rows.
 // ---------------------------------------------------------------------------
-template <typename T, int NPX>
+template <typename T, int NPX, int V = 0>
 __global__ void __launch_bounds__(1024) row2_kernel(const RowArgs<T> a, const cx<T>* __restrict__ tw) {
-    using P = IPlan<NPX>;
+    using P = IPlan<NPX, V>;
     constexpr int TL = P::TL;
     constexpr int HX = NPX / 3;
     constexpr int LS = line_stride(NPX);
@@ -40,6 +40,10 @@ __global__ void __launch_bounds__(1024) row2_kernel(const RowArgs<T> a, const cx
     const int nloop = TL < 32 ? ngroups : a.nlines;
     const T kx0 = a.kx0;
     constexpr int SUB1 = NPX / P::R1;
+    const cx<T>* colbase = a.colbase + (long long)blockIdx.y * a.tcol;
+    T* acc = a.acc + (long long)blockIdx.y * a.tacc;
+    cx<T>* out0 = a.out0 + (long long)blockIdx.y * a.tcol;
+    cx<T>* out1 = a.out1 ? a.out1 + (long long)blockIdx.y * a.tcol : nullptr;
 
     for (int zp = blockIdx.x; zp < a.npz; zp += gridDim.x) {
         // Phase A: Hermitian packing of two real fields fused into the first DIF stage.
@@ -48,8 +52,8 @@ __global__ void __launch_bounds__(1024) row2_kernel(const RowArgs<T> a, const cx
             const bool act = l < a.nlines;
             const int fa = act ? a.fa[l] : -1, fb = act ? a.fb[l] : -1;
             const bool da = act && ((a.dxa >> l) & 1u), db = act && ((a.dxb >> l) & 1u);
-            const cx<T>* pa = fa >= 0 ? a.colbase + (long long)fa * a.fstride + (long long)zp * HX : nullptr;
-            const cx<T>* pb = fb >= 0 ? a.colbase + (long long)fb * a.fstride + (long long)zp * HX : nullptr;
+            const cx<T>* pa = fa >= 0 ? colbase + (long long)fa * a.fstride + (long long)zp * HX : nullptr;
+            const cx<T>* pb = fb >= 0 ? colbase + (long long)fb * a.fstride + (long long)zp * HX : nullptr;
             // ms = m * SUB1 of the first stage (a compile-time constant after unrolling):
             // the zero band, and in most cases the direct / mirror choice, follow from it.
             auto ld = [&](int m, int ms) -> cx<T> {
@@ -78,7 +82,7 @@ __global__ void __launch_bounds__(1024) row2_kernel(const RowArgs<T> a, const cx
             const cx<T> v = lines[(s >> 1) * LS + pidx(p)];
             return (s & 1) ? v.y : v.x;
         };
-        T* accrow = a.acc + (long long)zp * NPX;
+        T* accrow = acc + (long long)zp * NPX;
         for (int p = threadIdx.x; p < NPX; p += blockDim.x) {
             if (a.kind == 0) {
                 const int r = a.r;
@@ -131,7 +135,7 @@ __global__ void __launch_bounds__(1024) row2_kernel(const RowArgs<T> a, const cx
 
         // Phase C: forward DIT of line 0 by the whole block; keep kx < nx/2.
         {
-            cx<T>* o0 = a.out0 + (long long)zp * HX;
+            cx<T>* o0 = out0 + (long long)zp * HX;
             if (a.kind == 0) {
                 P::template dit_blk<false, T>(lines, tw, threadIdx.x, blockDim.x, [&](int k, cx<T> v) {
                     if (k < HX) o0[k] = v;
@@ -140,7 +144,7 @@ __global__ void __launch_bounds__(1024) row2_kernel(const RowArgs<T> a, const cx
                 P::template dit_blk<false, T>(lines, tw, threadIdx.x, blockDim.x,
                                               [&](int k, cx<T> v) { lines[pidx(k)] = v; });
                 __syncthreads();
-                cx<T>* o1 = a.out1 + (long long)zp * HX;
+                cx<T>* o1 = out1 + (long long)zp * HX;
                 for (int k = threadIdx.x; k < HX; k += blockDim.x) {
                     const cx<T> X = lines[pidx(k)];
                     const cx<T> Y = cconj(lines[pidx(k == 0 ? 0 : NPX - k)]);
@@ -171,10 +175,10 @@ __device__ __forceinline__ void col2_store_tile(const cx<T>* sm, int per, cx<T>*
     }
 }
 
-template <typename T, int NPZ, int CB>
-__global__ void __launch_bounds__(CB * IPlan<NPZ>::TL < 32 ? 32 : CB * IPlan<NPZ>::TL)
+template <typename T, int NPZ, int CB, int V = 0>
+__global__ void __launch_bounds__(CB * IPlan<NPZ, V>::TL < 32 ? 32 : CB * IPlan<NPZ, V>::TL)
 col2_kernel(const ColArgs<T> a, const cx<T>* __restrict__ tw) {
-    using P = IPlan<NPZ>;
+    using P = IPlan<NPZ, V>;
     constexpr int TL = P::TL;
     constexpr int NZ = 2 * NPZ / 3;
     constexpr int LS = line_stride(NPZ);
@@ -187,6 +191,9 @@ col2_kernel(const ColArgs<T> a, const cx<T>* __restrict__ tw) {
     const bool valid = (g < CB) && (c < a.hx);
     const int cc = valid ? c : c0;
     const T kx = a.kx0 * (T)cc;
+    const long long oc = (long long)blockIdx.y * a.tcol;   // this tile's column-space fields
+    const long long os = (long long)blockIdx.y * a.tst;    // this tile's compact spectra
+    const T hh = a.hb ? a.hb[blockIdx.y] : a.h;
 
     if (a.kind == COL_FROM_STATE || a.kind == COL_PHI) {
         constexpr int PER = col_stride(LS + NZ);
@@ -195,7 +202,7 @@ col2_kernel(const ColArgs<T> a, const cx<T>* __restrict__ tw) {
         const int nsrc = a.kind == COL_FROM_STATE ? 2 : 1;
         for (int src = 0; src < nsrc; ++src) {
             if (a.kind == COL_FROM_STATE) {
-                const cx<T>* st = src == 0 ? a.st_eta : a.st_psi;
+                const cx<T>* st = (src == 0 ? a.st_eta : a.st_psi) + os;
                 for (int i = threadIdx.x; i < NZ * CB; i += blockDim.x) {
                     const int z = i / CB, cg = i - z * CB;
                     const int col = c0 + cg;
@@ -206,7 +213,7 @@ col2_kernel(const ColArgs<T> a, const cx<T>* __restrict__ tw) {
                 for (int i = threadIdx.x; i < NPZ * CB; i += blockDim.x) {
                     const int z = i / CB, cg = i - z * CB;
                     const int col = c0 + cg;
-                    sm[(size_t)cg * PER + pidx(z)] = col < a.hx ? a.pin[(long long)z * a.hx + col] : mk<T>(0, 0);
+                    sm[(size_t)cg * PER + pidx(z)] = col < a.hx ? a.pin[oc + (long long)z * a.hx + col] : mk<T>(0, 0);
                 }
                 __syncthreads();
                 // forward DIT: truncate to the kept modes, scale and taper into S
@@ -251,13 +258,13 @@ col2_kernel(const ColArgs<T> a, const cx<T>* __restrict__ tw) {
                     for (int i = 0; i < e2; ++i) f *= k2;          // |k|^(2 floor(a/2))
                     if (aa & 1) {                                  // odd a: one more G0 = |k| tanh(|k| h)
                         const T k = d_sqrt(k2);
-                        f *= k * tanh_kh(k * a.h);
+                        f *= k * tanh_kh(k * hh);
                     }
                     return cscale(s, f);
                 };
                 P::template dif<true, T>(line, tw, lt, bar, ld);
                 __syncthreads();
-                col2_store_tile<T, NPZ, CB>(sm, PER, a.colbase + (long long)a.out_f[o] * a.fstride, c0, a.hx);
+                col2_store_tile<T, NPZ, CB>(sm, PER, a.colbase + oc + (long long)a.out_f[o] * a.fstride, c0, a.hx);
                 __syncthreads();
             }
         }
@@ -272,8 +279,8 @@ col2_kernel(const ColArgs<T> a, const cx<T>* __restrict__ tw) {
         const int z = i / CB, cg = i - z * CB;
         const int col = c0 + cg;
         const bool in = col < a.hx;
-        sm[(size_t)cg * PER + pidx(z)] = in ? a.gin[(long long)z * a.hx + col] : mk<T>(0, 0);
-        sm[(size_t)cg * PER + LS + pidx(z)] = in ? a.nin[(long long)z * a.hx + col] : mk<T>(0, 0);
+        sm[(size_t)cg * PER + pidx(z)] = in ? a.gin[oc + (long long)z * a.hx + col] : mk<T>(0, 0);
+        sm[(size_t)cg * PER + LS + pidx(z)] = in ? a.nin[oc + (long long)z * a.hx + col] : mk<T>(0, 0);
     }
     __syncthreads();
     P::template dit<false, T>(l0, tw, lt, bar, [&](int k, cx<T> v) { l0[pidx(k)] = v; });
@@ -287,7 +294,7 @@ col2_kernel(const ColArgs<T> a, const cx<T>* __restrict__ tw) {
         const int ic = i / CB, cg = i - ic * CB;
         const int col = c0 + cg;
         if (col >= a.hx) continue;
-        const long long idx = (long long)ic * a.hx + col;
+        const long long idx = os + (long long)ic * a.hx + col;
         if (ic == NZ / 2) {
             if (a.mode == FIN_RHS) { a.ko_eta[idx] = mk<T>(0, 0); a.ko_psi[idx] = mk<T>(0, 0); }
             continue;
@@ -307,7 +314,7 @@ col2_kernel(const ColArgs<T> a, const cx<T>* __restrict__ tw) {
         cx<T> Fe = cscale(lc[pidx(ip)], s);
         const cx<T> Fp = cscale(lc[LS + pidx(ip)], s);
         const cx<T> se = a.s_eta[idx], sp = a.s_psi[idx];
-        const T G0 = k * tanh_kh(k * a.h);
+        const T G0 = k * tanh_kh(k * hh);
         if (col == 0 && mz == 0) Fe = mk<T>(0, 0);   // d eta/dt has zero mean
         cx<T> de = cadd(cscale(sp, G0), Fe);
         if (col == 0 && mz == 0) de = mk<T>(0, 0);
@@ -411,9 +418,10 @@ col2_kernel(const ColArgs<T> a, const cx<T>* __restrict__ tw) {
         if (threadIdx.x == 0) {
             double s0 = 0, s1 = 0, s2 = 0;
             for (int t = 0; t < (int)(blockDim.x >> 5); ++t) { s0 += red[0][t]; s1 += red[1][t]; s2 += red[2][t]; }
-            a.partial[3 * blockIdx.x + 0] = s0;
-            a.partial[3 * blockIdx.x + 1] = s1;
-            a.partial[3 * blockIdx.x + 2] = s2;
+            const long long pb = 3 * ((long long)blockIdx.y * gridDim.x + blockIdx.x);
+            a.partial[pb + 0] = s0;
+            a.partial[pb + 1] = s1;
+            a.partial[pb + 2] = s2;
         }
     }
 }

@@ -18,6 +18,8 @@ Generators
   Accuracy under Varying Nonlinearity"); psi is the textbook second-order
   Stokes potential evaluated on the surface.
 * ``gaussian_bump`` - the tank's initial bump of Sec. 8 ("Wave Propagation").
+* ``batch_tiles``  - the per-tile parameters (grid, depth, order, Hs, Tp, seed)
+  of the mixed batch of independent sea tiles.
 
 Random phases come from splitmix64 (S. Vigna's published 64-bit mixer) keyed
 by (seed, linear mode index), so a mode's phase does not depend on the grid
@@ -209,3 +211,29 @@ def gaussian_bump(nx: int, nz: int, Lx: float, Lz: float, A: float, sigma: float
     r = np.hypot(X - Lx / 2, Z - Lz / 2)
     eta = np.where(r < R, A * np.exp(-r * r / (2 * sigma * sigma)), 0.0)
     return eta, np.zeros_like(eta)
+
+
+def batch_tiles(counts=((128, 40), (256, 32), (512, 16), (1024, 8)), dx: float = 0.78125,
+                orders=(3, 4, 5, 6), seed0: int = 1000, g: float = 9.81, max_steepness: float = 0.1):
+    """Tile list of the mixed batch: tile t draws Hs ~ U[0.5, 4], h ~ U[10, 100],
+    Tp ~ U[6, 12] from the counter-based generator with seed seed0 + t; orders
+    cycle through `orders` within each size. Hs is clipped so that
+    k_ref Hs / 2 <= max_steepness, with k_ref = max(k_p, 2 pi / L): on tiles
+    shorter than the peak wavelength only the spectral tail is resolved and the
+    grid normalisation puts all of Hs there. Returns dicts with nx, nz, Lx, Lz,
+    h, M, Hs, Tp, seed."""
+    tiles = []
+    t = 0
+    for n, cnt in counts:
+        L = n * dx
+        for j in range(cnt):
+            seed = seed0 + t
+            u = uniform01(seed, np.arange(3, dtype=np.uint64))
+            Hs = 0.5 + 3.5 * float(u[0])
+            h = 10.0 + 90.0 * float(u[1])
+            Tp = 6.0 + 6.0 * float(u[2])
+            kref = max(peak_wavenumber(Tp, h, g), 2 * math.pi / L)
+            Hs = min(Hs, 2 * max_steepness / kref)
+            tiles.append(dict(nx=n, nz=n, Lx=L, Lz=L, h=h, M=orders[j % len(orders)], Hs=Hs, Tp=Tp, seed=seed))
+            t += 1
+    return tiles

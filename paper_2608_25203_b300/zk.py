@@ -27,6 +27,9 @@ EXPORTS = [
     "zk_rhs", "zk_dno", "zk_step", "zk_energy", "zk_sync", "zk_device_bytes",
     "zk_launches_per_step", "zk_profile_step", "zk_dno_static", "zk_dno_inverse", "zk_relax",
     "zk_set_state_tank", "zk_get_state_tank",
+    "zk_batch_create", "zk_batch_destroy", "zk_batch_set_options", "zk_batch_set_state", "zk_batch_get_state",
+    "zk_batch_energy", "zk_batch_step", "zk_batch_sync", "zk_batch_info", "zk_batch_group", "zk_batch_set_shape",
+    "zk_batch_autotune",
     "zk_strerror", "zk_version",
 ]
 
@@ -77,6 +80,19 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "zk_set_state_tank": ([vp, vp, vp, i, i], i),
         "zk_get_state_tank": ([vp, vp, vp, i, i], i),
         "zk_relax": ([vp, vp, vp, i, i, d, i], i),
+        "zk_batch_create": ([ctypes.POINTER(vp), i, ctypes.POINTER(i), ctypes.POINTER(i), pd, pd, pd, d,
+                             ctypes.POINTER(i), i], i),
+        "zk_batch_destroy": ([vp], None),
+        "zk_batch_set_options": ([vp, ctypes.POINTER(ZkOptions)], i),
+        "zk_batch_set_state": ([vp, i, vp, vp, i, i], i),
+        "zk_batch_get_state": ([vp, i, vp, vp, i, i], i),
+        "zk_batch_energy": ([vp, i, pd, pd, pd, pd], i),
+        "zk_batch_step": ([vp, d, i], i),
+        "zk_batch_sync": ([vp], i),
+        "zk_batch_info": ([vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(ctypes.c_size_t)], i),
+        "zk_batch_group": ([vp, i] + [ctypes.POINTER(i)] * 7, i),
+        "zk_batch_set_shape": ([vp, i, i, i, i], i),
+        "zk_batch_autotune": ([vp, d, ctypes.c_char_p, ctypes.POINTER(i), ctypes.POINTER(i)], i),
         "zk_strerror": ([i], ctypes.c_char_p),
         "zk_version": ([], ctypes.c_char_p),
     }
@@ -317,3 +333,135 @@ class Zakharov:
 
     def sync(self):
         zk_sync(self.ctx)
+
+
+# ---- batched tiles ----------------------------------------------------------
+def zk_batch_create(nx, nz, Lx, Lz, h, g, M, precision=ZK_F32):
+    n = len(nx)
+    if not all(len(v) == n for v in (nz, Lx, Lz, h, M)):
+        raise ValueError("per-tile lists must have equal length")
+    ia = lambda v: (ctypes.c_int * n)(*[int(x) for x in v])
+    da = lambda v: (ctypes.c_double * n)(*[float(x) for x in v])
+    b = ctypes.c_void_p()
+    _check("zk_batch_create", load().zk_batch_create(ctypes.byref(b), n, ia(nx), ia(nz), da(Lx), da(Lz), da(h),
+                                                     float(g), ia(M), precision))
+    return b
+
+
+def zk_batch_destroy(b):
+    load().zk_batch_destroy(b)
+
+
+def zk_batch_set_options(b, eps=1.0, integrator=ZK_RK4, taper=1, filter=1, stream=None):
+    o = ZkOptions(eps, integrator, taper, filter, stream)
+    _check("zk_batch_set_options", load().zk_batch_set_options(b, ctypes.byref(o)))
+
+
+def zk_batch_set_state(b, tile, eta, psi, dtype=None):
+    dt = dtype if dtype is not None else _dtype_of(eta)
+    pe, de = _ptr(eta, dt)
+    pp, dp = _ptr(psi, dt)
+    if de != dp:
+        raise ValueError("eta and psi must both be host or both device arrays")
+    _check("zk_batch_set_state", load().zk_batch_set_state(b, int(tile), pe, pp, dt, de))
+
+
+def zk_batch_get_state(b, tile, eta, psi, dtype=None):
+    dt = dtype if dtype is not None else _dtype_of(eta)
+    pe, de = _ptr(eta, dt)
+    pp, _ = _ptr(psi, dt)
+    _check("zk_batch_get_state", load().zk_batch_get_state(b, int(tile), pe, pp, dt, de))
+
+
+def zk_batch_energy(b, tile):
+    v = [ctypes.c_double() for _ in range(4)]
+    _check("zk_batch_energy", load().zk_batch_energy(b, int(tile), *[ctypes.byref(x) for x in v]))
+    return tuple(x.value for x in v)
+
+
+def zk_batch_step(b, dt, n=1):
+    _check("zk_batch_step", load().zk_batch_step(b, float(dt), int(n)))
+
+
+def zk_batch_sync(b):
+    _check("zk_batch_sync", load().zk_batch_sync(b))
+
+
+def zk_batch_info(b):
+    ng, nl, by = ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t()
+    _check("zk_batch_info", load().zk_batch_info(b, ctypes.byref(ng), ctypes.byref(nl), ctypes.byref(by)))
+    return ng.value, nl.value, by.value
+
+
+def zk_batch_group(b, gi):
+    v = [ctypes.c_int() for _ in range(7)]
+    _check("zk_batch_group", load().zk_batch_group(b, int(gi), *[ctypes.byref(x) for x in v]))
+    return dict(zip(("nx", "nz", "M", "ntiles", "plan_v", "col_ci", "row_occ"), (x.value for x in v)))
+
+
+def zk_batch_set_shape(b, gi, plan_v, col_ci, row_occ):
+    _check("zk_batch_set_shape", load().zk_batch_set_shape(b, int(gi), int(plan_v), int(col_ci), int(row_occ)))
+
+
+def zk_batch_autotune(b, dt, cache_path=None):
+    t, c = ctypes.c_int(), ctypes.c_int()
+    path = cache_path.encode() if cache_path else None
+    _check("zk_batch_autotune", load().zk_batch_autotune(b, float(dt), path, ctypes.byref(t), ctypes.byref(c)))
+    return t.value, c.value
+
+
+class Batch:
+    """Many independent tiles advanced together (one graph, one launch per pass of each group)."""
+
+    def __init__(self, tiles, g=9.81, precision=ZK_F32, eps=1.0, integrator=ZK_RK4, stream=None):
+        """tiles: list of dicts with nx, nz, Lx, Lz, h, M."""
+        self.tiles = [dict(t) for t in tiles]
+        col = lambda k: [t[k] for t in self.tiles]
+        self.b = zk_batch_create(col("nx"), col("nz"), col("Lx"), col("Lz"), col("h"), g, col("M"), precision)
+        self.precision = precision
+        zk_batch_set_options(self.b, eps=eps, integrator=integrator, stream=stream)
+
+    def close(self):
+        if self.b is not None:
+            zk_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_state(self, tile, eta, psi):
+        if isinstance(eta, np.ndarray):
+            eta = np.ascontiguousarray(eta)
+            psi = np.ascontiguousarray(psi, dtype=eta.dtype)
+        zk_batch_set_state(self.b, tile, eta, psi)
+
+    def get_state(self, tile, dtype=np.float64):
+        t = self.tiles[tile]
+        e = np.empty((t["nz"], t["nx"]), dtype)
+        p = np.empty((t["nz"], t["nx"]), dtype)
+        zk_batch_get_state(self.b, tile, e, p)
+        return e, p
+
+    def step(self, dt, n=1):
+        zk_batch_step(self.b, dt, n)
+
+    def sync(self):
+        zk_batch_sync(self.b)
+
+    def energy(self, tile):
+        return zk_batch_energy(self.b, tile)
+
+    def info(self):
+        return zk_batch_info(self.b)
+
+    def groups(self):
+        return [zk_batch_group(self.b, gi) for gi in range(self.info()[0])]
+
+    def set_shape(self, gi, plan_v, col_ci, row_occ):
+        zk_batch_set_shape(self.b, gi, plan_v, col_ci, row_occ)
+
+    def autotune(self, dt, cache_path=None):
+        return zk_batch_autotune(self.b, dt, cache_path)
