@@ -242,6 +242,65 @@ zk_status zk_batch_set_shape(zk_batch *b, int gi, int plan_v, int col_ci, int ro
  * Blocks until done. */
 zk_status zk_batch_autotune(zk_batch *b, double dt, const char *cache_path, int *tuned, int *cached);
 
+/* ---- Learned closure (library addition; the paper has no learned component) ----
+ *
+ * A small network corrects the order-b right-hand side towards the order-M
+ * one of the same context (Sec. 3.2 series, Eq. 9, truncated at b and M
+ * terms): f_closure = f_b + R_hat, where R is the network's prediction of the
+ * physical residual f_M - f_b of both equations (Eqs. 4 and 10) and R_hat its
+ * spectrum with the Nyquist modes zero, the taper of the nonlinear terms
+ * applied and the mean of d eta / dt kept at zero.
+ *
+ * Network (zk_net): x [B][6][H][W] -> 3x3 conv 6->32, tanh -> 3x3 conv 32->32,
+ * tanh -> 3x3 conv 32->32, tanh -> 1x1 conv 32->2 -> y [B][2][H][W]; periodic
+ * convolutions (cross-correlation, wrap-around at the edges); weights and the
+ * activations entering each convolution rounded to FP16, FP32 arithmetic.
+ * Parameters: one FP32 vector W1 b1 W2 b2 W3 b3 W4 b4, weights [out][in][k][k]
+ * (20322 values). H, W: multiples of 16. All tensors are device FP32 arrays
+ * owned by the caller; the network keeps its own activations for one
+ * backward pass. Work is queued on `stream` (cudaStream_t, NULL = legacy
+ * default); calls that return a host value synchronise it. */
+typedef struct zk_net zk_net;
+/* cin, width, cout must be 6, 32, 2 (ZK_EUNSUPPORTED otherwise); parameters start at zero. */
+zk_status zk_net_create(zk_net **out, int cin, int width, int cout);
+void zk_net_destroy(zk_net *n);
+zk_status zk_net_param_count(const zk_net *n, int *count);
+/* Replace the parameters (host or device FP32 vector); resets the Adam moments. */
+zk_status zk_net_set_params(zk_net *n, const float *theta, int on_device);
+zk_status zk_net_get_params(zk_net *n, float *theta, int on_device);
+/* y = net(x) for `batch` samples of nz x nx; y may be NULL. Keeps what backward needs. */
+zk_status zk_net_forward(zk_net *n, const float *x, float *y, int batch, int nz, int nx, void *stream);
+/* Given dL/dy of the last forward pass: dL/dtheta into grad (device, may be NULL:
+ * kept inside for zk_net_adam) and dL/dx into dx (may be NULL). ZK_ESTATE
+ * before any forward pass. */
+zk_status zk_net_backward(zk_net *n, const float *dy, float *grad, float *dx, void *stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) with the
+ * given device gradient, or the one the last backward pass kept (grad NULL). */
+zk_status zk_net_adam(zk_net *n, const float *grad, double lr, void *stream);
+/* forward, mean-squared error against target (same shape as y), backward and
+ * one Adam step; *loss (may be NULL) receives the loss before the update. */
+zk_status zk_net_train_step(zk_net *n, const float *x, const float *target, int batch, int nz, int nx, double lr,
+                            double *loss, void *stream);
+/* Training pair at the context's current state (FP32 contexts): feat [6][nz][nx]
+ * = eta, d_x eta, d_z eta, G0 psi, (d eta/dt)_b - G0 psi, (d psi/dt)_b + g eta,
+ * each divided by in_scale[c] (NULL: 1); target [2][nz][nx] (may be NULL) =
+ * f_M - f_b divided by out_scale (NULL: 1). 1 <= b < M. Device outputs; syncs. */
+zk_status zk_closure_features(zk_ctx *ctx, int base_order, const float *in_scale, const float *out_scale, float *feat,
+                              float *target);
+/* Attach net (NULL detaches) to an FP32 context with the scales it was trained
+ * with. From then on zk_step (RK4 only; ZK_EUNSUPPORTED for IF-AB2), zk_rhs and
+ * zk_dno use f_closure. Every check_every steps (0 = never), before the step,
+ * the context computes f_M and f_b at the current state and the relative L2
+ * error of the predicted residual against f_M - f_b; above check_tol the
+ * closure is switched off for good and the context steps at order M (the
+ * fallback). Checks synchronise the stream. The caller keeps net alive while
+ * attached. */
+zk_status zk_closure_set(zk_ctx *ctx, zk_net *net, int base_order, const float *in_scale, const float *out_scale,
+                         int check_every, double check_tol);
+/* active: 1 while the closure is in use; checks made; the step count at which
+ * it fell back (-1: never); the error of the last check (-1: none yet). */
+zk_status zk_closure_status(const zk_ctx *ctx, int *active, int *checks, long long *fallback_step, double *last_err);
+
 /* Static text for a status code. */
 const char *zk_strerror(zk_status s);
 

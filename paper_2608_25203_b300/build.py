@@ -1,6 +1,6 @@
 """Build the sm_103a shared library in-tree (nvcc, no torch extension machinery).
 
-``build()`` compiles ``csrc/zk_api.cu`` into ``libzk.so`` next to this file.
+``build()`` compiles the ``csrc/*.cu`` translation units into ``libzk.so`` next to this file.
 The library exports the C ABI of ``include/zk.h`` and links the CUDA runtime
 statically, so it loads with nothing but the driver.
 """
@@ -14,8 +14,8 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libzk.so")
-SOURCES = [os.path.join(HERE, "csrc", "zk_api.cu"), os.path.join(HERE, "csrc", "zk_static.cu")]
-DEPS = SOURCES + [os.path.join(HERE, "csrc", f) for f in ("zk_fft.cuh", "zk_kernels.cuh", "zk_fft2.cuh", "zk_kernels2.cuh")] + \
+SOURCES = [os.path.join(HERE, "csrc", f) for f in ("zk_api.cu", "zk_static.cu", "zk_net.cu")]
+DEPS = SOURCES + [os.path.join(HERE, "csrc", f) for f in ("zk_fft.cuh", "zk_kernels.cuh", "zk_fft2.cuh", "zk_kernels2.cuh", "zk_net_internal.h")] + \
     [os.path.join(ROOT, "include", "zk.h")]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

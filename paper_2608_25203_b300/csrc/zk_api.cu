@@ -20,6 +20,7 @@
 
 #include "../../include/zk.h"
 #include "zk_kernels2.cuh"
+#include "zk_net_internal.h"
 
 using namespace zk;
 
@@ -104,6 +105,23 @@ struct zk_ctx {
     // launch shape (set by the batch autotuner): plan variant, columns-per-block
     // choice (0 / 1 / 2 = half / default / double), row blocks per SM (0 = all resident)
     int plan_v = 0, col_ci = 1, row_occ = 0;
+    int m_run = 0;                         // order of the right-hand side being enqueued (<= M)
+    // learned closure (FP32): order-base_M right-hand side plus the network's residual
+    zk_net* net = nullptr;
+    bool closure_on = false;
+    int base_M = 2;
+    ClosureScales sc{};
+    int check_every = 0;
+    double check_tol = 0.2;
+    int nchecks = 0;
+    long long nsteps = 0;                  // steps taken since the closure was set
+    long long fallback_step = -1;
+    double last_err = -1.0;
+    void* cspec = nullptr;                 // 6 compact spectra (features, then the residual)
+    void* feat = nullptr;                  // [6][nz][nx] FP32 features
+    void* rbuf = nullptr;                  // [2][nz][nx] FP32 network output
+    void* chk = nullptr;                   // 2 compact spectra: the high-order right-hand side
+    double* cpart = nullptr;               // check partial sums
     void *y_eta = nullptr, *y_psi = nullptr, *ys_eta = nullptr, *ys_psi = nullptr;
     void *ka_eta = nullptr, *ka_psi = nullptr, *ko_eta = nullptr, *ko_psi = nullptr;
     void *h_eta = nullptr, *h_psi = nullptr;   // IF-AB2 forcing history
@@ -137,6 +155,7 @@ struct zk_ctx {
 namespace {
 
 cudaStream_t user_stream(const zk_ctx* c) { return (cudaStream_t)c->opt.stream; }
+void drop_graph(zk_ctx* c);
 
 zk_status cu(cudaError_t e) { return e == cudaSuccess ? ZK_OK : ZK_ECUDA; }
 
@@ -395,7 +414,7 @@ struct Pipe {
         std::memset(&a, 0, sizeof(a));
         a.colbase = C(c->col);
         a.fstride = c->fstride;
-        a.M = c->M;
+        a.M = c->m_run > 0 ? c->m_run : c->M;
         a.eps = (T)c->opt.eps;
         double p = 1.0;
         for (int j = 0; j < kMaxOrder + 3; ++j) { a.epsp[j] = (T)p; p *= c->opt.eps; }
@@ -438,8 +457,8 @@ struct Pipe {
     }
 
     static cudaError_t rhs(zk_ctx* c, const cx<T>* se, const cx<T>* sp, ColArgs<T> fin, cudaStream_t s, int* nlaunch) {
-        const Fields F{c->M};
-        const int M = c->M;
+        const int M = c->m_run > 0 ? c->m_run : c->M;
+        const Fields F{M};
         const double U = (double)c->fstride * sizeof(cx<T>);                 // one column-space field
         const double Cc = (double)c->nz * c->hx * sizeof(cx<T>);             // one compact spectrum
         const double Pp = (double)c->npz * c->npx * sizeof(T);               // the padded accumulator
@@ -564,6 +583,158 @@ struct Pipe {
         return cudaSuccess;
     }
 
+    // ---- learned closure (FP32 contexts) -------------------------------------
+    // Residual spectra R_hat (unnormalised, both components) into cspec[0..1]
+    // from the state (se, sp) and the low-order right-hand side held in ko.
+    static cudaError_t closure_residual(zk_ctx* c, const cx<T>* se, const cx<T>* sp, cudaStream_t s, int* nl) {
+        const long long n = (long long)c->nz * c->hx;
+        cx<T>* cs = C(c->cspec);
+        closure_prep_kernel<T><<<4 * 148, 256, 0, s>>>(se, sp, C(c->ko_eta), C(c->ko_psi), cs, c->nz, c->hx,
+                                                       (T)(2.0 * M_PI / c->Lx), (T)(2.0 * M_PI / c->Lz), (T)c->h,
+                                                       (T)c->g, c->sc);
+        cudaError_t e = cudaGetLastError();
+        float* f = reinterpret_cast<float*>(c->feat);
+        const size_t plane = (size_t)c->nx * c->nz;
+        for (int k = 0; k < 3 && e == cudaSuccess; ++k)
+            e = to_physical(c, cs + 2 * k * n, cs + (2 * k + 1) * n, f + 2 * k * plane, f + (2 * k + 1) * plane, ZK_F32, s);
+        const float* y = nullptr;
+        if (e == cudaSuccess) e = zk_net_infer(c->net, f, &y, 1, c->nz, c->nx, s);
+        const cx<T>* twx = reinterpret_cast<const cx<T>*>(c->tw_x);
+        const cx<T>* twz = reinterpret_cast<const cx<T>*>(c->tw_z);
+        if (e == cudaSuccess) e = launch_rows_fwd<T, float>(c->nx, y, y + plane, c->nz, cs, cs + n, twx, s);
+        if (e == cudaSuccess) e = launch_cols<T, false>(c->nz, cs, cs + n, c->hx, twz, s);
+        if (nl) *nl += 1 + 6 + 4 + 2;
+        return e;
+    }
+
+    // One closure right-hand side at (se, sp): order-base_M right-hand side,
+    // the residual, and the combination/epilogue of `fin` (mode set by the caller).
+    static cudaError_t closure_stage(zk_ctx* c, const cx<T>* se, const cx<T>* sp, ColArgs<T> fin, cudaStream_t s, int* nl) {
+        ColArgs<T> r = col_base(c);
+        r.mode = FIN_RHS;
+        r.ko_eta = C(c->ko_eta);
+        r.ko_psi = C(c->ko_psi);
+        const int save = c->m_run;
+        c->m_run = c->base_M;
+        cudaError_t e = rhs(c, se, sp, r, s, nl);
+        c->m_run = save;
+        if (e == cudaSuccess) e = closure_residual(c, se, sp, s, nl);
+        if (e == cudaSuccess) {
+            const long long n = (long long)c->nz * c->hx;
+            fin.ko_eta = C(c->ko_eta);
+            fin.ko_psi = C(c->ko_psi);
+            closure_combine_kernel<T><<<4 * 148, 256, 0, s>>>(fin, C(c->cspec), C(c->cspec) + n, c->sc);
+            e = cudaGetLastError();
+            if (nl) ++*nl;
+        }
+        return e;
+    }
+
+    static cudaError_t closure_rk4_step(zk_ctx* c, double dt, cudaStream_t s, int* nlaunch) {
+        for (int st = 1; st <= 4; ++st) {
+            ColArgs<T> fin = col_base(c);
+            fin.mode = st;
+            fin.dt = (T)dt;
+            fin.y_eta = C(c->y_eta); fin.y_psi = C(c->y_psi);
+            fin.ys_eta = C(c->ys_eta); fin.ys_psi = C(c->ys_psi);
+            fin.ka_eta = C(c->ka_eta); fin.ka_psi = C(c->ka_psi);
+            const cx<T>* se = st == 1 ? C(c->y_eta) : C(c->ys_eta);
+            const cx<T>* sp = st == 1 ? C(c->y_psi) : C(c->ys_psi);
+            cudaError_t e = closure_stage(c, se, sp, fin, s, nlaunch);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
+
+    // Fallback check at the current state: relative L2 error of the predicted
+    // residual against f_M - f_base (both components); past check_tol the
+    // closure is switched off and the context steps at order M from then on.
+    static zk_status closure_check(zk_ctx* c, cudaStream_t s) {
+        const long long n = (long long)c->nz * c->hx;
+        const size_t compact = (size_t)n * sizeof(cx<T>);
+        ColArgs<T> r = col_base(c);
+        r.mode = FIN_RHS;
+        r.ko_eta = C(c->ko_eta);
+        r.ko_psi = C(c->ko_psi);
+        const int save = c->m_run;
+        c->m_run = c->M;
+        cudaError_t e = rhs(c, C(c->y_eta), C(c->y_psi), r, s, nullptr);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(c->chk, c->ko_eta, compact, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync((char*)c->chk + compact, c->ko_psi, compact, cudaMemcpyDeviceToDevice, s);
+        c->m_run = c->base_M;
+        if (e == cudaSuccess) e = rhs(c, C(c->y_eta), C(c->y_psi), r, s, nullptr);
+        c->m_run = save;
+        if (e == cudaSuccess) e = closure_residual(c, C(c->y_eta), C(c->y_psi), s, nullptr);
+        constexpr int nb = 256;
+        if (e == cudaSuccess) {
+            const double dmax = std::max(c->Lx / c->nx, c->Lz / c->nz);
+            closure_err_kernel<T><<<nb, 256, 0, s>>>(C(c->chk), C(c->chk) + n, C(c->ko_eta), C(c->ko_psi), C(c->cspec),
+                                                     C(c->cspec) + n, c->nz, c->hx, (T)(2.0 * M_PI / c->Lx),
+                                                     (T)(2.0 * M_PI / c->Lz), (T)(2.0 / 3.0 * M_PI / dmax),
+                                                     c->opt.taper, c->sc, c->cpart);
+            e = cudaGetLastError();
+        }
+        std::vector<double> hp(2 * nb);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hp.data(), c->cpart, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return ZK_ECUDA;
+        double num = 0.0, den = 0.0;
+        for (int i = 0; i < nb; ++i) { num += hp[2 * i]; den += hp[2 * i + 1]; }
+        const double err = den > 0.0 ? std::sqrt(num / den) : 0.0;
+        c->last_err = err;
+        ++c->nchecks;
+        if (!(err <= c->check_tol)) {
+            c->closure_on = false;
+            c->fallback_step = c->nsteps;
+            drop_graph(c);
+        }
+        return ZK_OK;
+    }
+
+    // Training pairs at the current state: features (6 physical channels,
+    // divided by in_scale) and, when tgt is non-null, the residual f_M - f_base
+    // (2 physical channels, divided by out_scale). Device FP32 outputs.
+    static cudaError_t closure_features(zk_ctx* c, float* feat, float* tgt, cudaStream_t s) {
+        const long long n = (long long)c->nz * c->hx;
+        const size_t compact = (size_t)n * sizeof(cx<T>);
+        const size_t plane = (size_t)c->nx * c->nz;
+        ColArgs<T> r = col_base(c);
+        r.mode = FIN_RHS;
+        r.ko_eta = C(c->ko_eta);
+        r.ko_psi = C(c->ko_psi);
+        const int save = c->m_run;
+        cudaError_t e = cudaSuccess;
+        if (tgt) {
+            c->m_run = c->M;
+            e = rhs(c, C(c->y_eta), C(c->y_psi), r, s, nullptr);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(c->chk, c->ko_eta, compact, cudaMemcpyDeviceToDevice, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync((char*)c->chk + compact, c->ko_psi, compact, cudaMemcpyDeviceToDevice, s);
+        }
+        c->m_run = c->base_M;
+        if (e == cudaSuccess) e = rhs(c, C(c->y_eta), C(c->y_psi), r, s, nullptr);
+        c->m_run = save;
+        cx<T>* cs = C(c->cspec);
+        if (e == cudaSuccess && tgt) {
+            // the difference kernel reads each pair as one contiguous [eta | psi] block
+            e = cudaMemcpyAsync(cs + 2 * n, c->ko_eta, compact, cudaMemcpyDeviceToDevice, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(cs + 3 * n, c->ko_psi, compact, cudaMemcpyDeviceToDevice, s);
+            if (e == cudaSuccess) {
+                closure_diff_kernel<T><<<4 * 148, 256, 0, s>>>(C(c->chk), cs + 2 * n, cs, n, c->sc);
+                e = cudaGetLastError();
+            }
+            if (e == cudaSuccess) e = to_physical(c, cs, cs + n, tgt, tgt + plane, ZK_F32, s);
+        }
+        if (e == cudaSuccess) {
+            closure_prep_kernel<T><<<4 * 148, 256, 0, s>>>(C(c->y_eta), C(c->y_psi), C(c->ko_eta), C(c->ko_psi), cs, c->nz,
+                                                           c->hx, (T)(2.0 * M_PI / c->Lx), (T)(2.0 * M_PI / c->Lz),
+                                                           (T)c->h, (T)c->g, c->sc);
+            e = cudaGetLastError();
+        }
+        for (int k = 0; k < 3 && e == cudaSuccess; ++k)
+            e = to_physical(c, cs + 2 * k * n, cs + (2 * k + 1) * n, feat + 2 * k * plane, feat + (2 * k + 1) * plane, ZK_F32, s);
+        return e;
+    }
+
     static cudaError_t ifab2_step(zk_ctx* c, double dt, bool first, cudaStream_t s, int* nlaunch) {
         ColArgs<T> fin = col_base(c);
         fin.mode = FIN_IFAB2;
@@ -613,6 +784,7 @@ struct Pipe {
         fin.mode = FIN_RHS;
         fin.ko_eta = C(c->ko_eta);
         fin.ko_psi = C(c->ko_psi);
+        if (c->closure_on) return closure_stage(c, C(c->y_eta), C(c->y_psi), fin, s, nullptr);
         return rhs(c, C(c->y_eta), C(c->y_psi), fin, s, nullptr);
     }
 
@@ -714,8 +886,10 @@ void drop_graph(zk_ctx* c) {
 
 // variant: 0 = RK4 step, 1 = IF-AB2 bootstrap step, 2 = IF-AB2 step with history
 cudaError_t enqueue_step_any(zk_ctx* c, double dt, cudaStream_t s, int* nl, int variant) {
-    if (variant == 0)
+    if (variant == 0) {
+        if (c->closure_on && c->prec == ZK_F32) return Pipe<float>::closure_rk4_step(c, dt, s, nl);
         return c->prec == ZK_F32 ? Pipe<float>::rk4_step(c, dt, s, nl) : Pipe<double>::rk4_step(c, dt, s, nl);
+    }
     const bool first = variant == 1;
     return c->prec == ZK_F32 ? Pipe<float>::ifab2_step(c, dt, first, s, nl)
                              : Pipe<double>::ifab2_step(c, dt, first, s, nl);
@@ -822,7 +996,7 @@ zk_status ctx_create(zk_ctx** out, int nx, int nz, double Lx, double Lz, const d
     zk_ctx* c = new (std::nothrow) zk_ctx();
     if (!c) return ZK_ENOMEM;
     c->nx = nx; c->nz = nz; c->npx = 3 * nx / 2; c->npz = 3 * nz / 2; c->hx = nx / 2;
-    c->Lx = Lx; c->Lz = Lz; c->h = h[0]; c->g = g; c->M = M; c->prec = precision;
+    c->Lx = Lx; c->Lz = Lz; c->h = h[0]; c->g = g; c->M = M; c->m_run = M; c->prec = precision;
     c->opt.eps = 1.0; c->opt.integrator = ZK_RK4; c->opt.taper = 1; c->opt.filter = 1; c->opt.stream = nullptr;
     c->nb = nb;
     c->hv.assign(h, h + nb);
@@ -1077,13 +1251,17 @@ zk_status zk_relax(zk_ctx* c, const void* sigma, const void* eta_target, int dty
 zk_status zk_step(zk_ctx* c, double dt, int n) {
     if (!c || n < 0 || !(dt > 0) || !std::isfinite(dt)) return ZK_EINVAL;
     if (!c->has_state) return ZK_ESTATE;
-    if (n == 0) return ZK_OK;
-    if (!c->gvalid || c->gdt != dt) {
-        zk_status st = build_graph(c, dt);
-        if (st != ZK_OK) return st;
-    }
+    if (c->closure_on && c->opt.integrator != ZK_RK4) return ZK_EUNSUPPORTED;
     cudaStream_t s = user_stream(c);
     for (int i = 0; i < n; ++i) {
+        if (c->closure_on && c->check_every > 0 && c->nsteps % c->check_every == 0) {
+            zk_status st = Pipe<float>::closure_check(c, s);   // may switch the closure off
+            if (st != ZK_OK) return st;
+        }
+        if (!c->gvalid || c->gdt != dt) {
+            zk_status st = build_graph(c, dt);
+            if (st != ZK_OK) return st;
+        }
         cudaGraphExec_t g = c->gexec;
         if (c->opt.integrator == ZK_IFAB2 && !(c->ab_valid && c->ab_dt == dt)) {
             // first step, or a step whose dt differs from the history's: IF-Euler (Sec. 3.4)
@@ -1092,6 +1270,7 @@ zk_status zk_step(zk_ctx* c, double dt, int n) {
             c->ab_dt = dt;
         }
         if (cudaGraphLaunch(g, s) != cudaSuccess) return ZK_ECUDA;
+        ++c->nsteps;
     }
     return ZK_OK;
 }
@@ -1189,7 +1368,86 @@ zk_status zk_device_bytes(const zk_ctx* c, size_t* b) {
 
 zk_status zk_launches_per_step(const zk_ctx* c, int* n) {
     if (!c || !n) return ZK_EINVAL;
-    *n = (c->opt.integrator == ZK_IFAB2 ? 1 : 4) * (2 * c->M + 1);
+    *n = c->gvalid ? c->launches_per_step : (c->opt.integrator == ZK_IFAB2 ? 1 : 4) * (2 * c->M + 1);
+    return ZK_OK;
+}
+
+static zk_status closure_buffers(zk_ctx* c) {
+    if (c->cspec) return ZK_OK;
+    const size_t compact = (size_t)c->nz * c->hx * c->csz, plane = (size_t)c->nx * c->nz * sizeof(float);
+    zk_status st = dalloc(c, &c->cspec, 6 * compact);
+    if (st == ZK_OK) st = dalloc(c, &c->feat, 6 * plane);
+    if (st == ZK_OK) st = dalloc(c, &c->chk, 2 * compact);
+    if (st == ZK_OK) st = dalloc(c, (void**)&c->cpart, 2 * 256 * sizeof(double));
+    return st;
+}
+
+static void set_scales(zk_ctx* c, const float* in_scale, const float* out_scale) {
+    for (int i = 0; i < 6; ++i) c->sc.in[i] = in_scale ? in_scale[i] : 1.0f;
+    for (int i = 0; i < 2; ++i) c->sc.out[i] = out_scale ? out_scale[i] : 1.0f;
+}
+
+static bool scales_ok(const float* in_scale, const float* out_scale) {
+    for (int i = 0; in_scale && i < 6; ++i) if (!(in_scale[i] > 0.0f) || !std::isfinite(in_scale[i])) return false;
+    for (int i = 0; out_scale && i < 2; ++i) if (!(out_scale[i] > 0.0f) || !std::isfinite(out_scale[i])) return false;
+    return true;
+}
+
+zk_status zk_closure_features(zk_ctx* c, int base_order, const float* in_scale, const float* out_scale, float* feat,
+                              float* target) {
+    if (!c || !feat || base_order < 1 || base_order >= c->M || !scales_ok(in_scale, out_scale)) return ZK_EINVAL;
+    if (c->prec != ZK_F32) return ZK_EUNSUPPORTED;
+    if (!c->has_state) return ZK_ESTATE;
+    zk_status st = closure_buffers(c);
+    if (st != ZK_OK) return st;
+    const ClosureScales keep = c->sc;
+    const int keep_base = c->base_M;
+    set_scales(c, in_scale, out_scale);
+    c->base_M = base_order;
+    cudaStream_t s = user_stream(c);
+    cudaError_t e = Pipe<float>::closure_features(c, feat, target, s);
+    c->sc = keep;
+    c->base_M = keep_base;
+    if (e != cudaSuccess) return ZK_ECUDA;
+    return cu(cudaStreamSynchronize(s));
+}
+
+zk_status zk_closure_set(zk_ctx* c, zk_net* net, int base_order, const float* in_scale, const float* out_scale,
+                         int check_every, double check_tol) {
+    if (!c) return ZK_EINVAL;
+    if (!net) {
+        c->closure_on = false;
+        c->net = nullptr;
+        drop_graph(c);
+        return ZK_OK;
+    }
+    if (base_order < 1 || base_order >= c->M || check_every < 0 || !(check_tol > 0) || !in_scale || !out_scale ||
+        !scales_ok(in_scale, out_scale))
+        return ZK_EINVAL;
+    if (c->prec != ZK_F32) return ZK_EUNSUPPORTED;
+    zk_status st = closure_buffers(c);
+    if (st == ZK_OK) st = zk_net_reserve(net, (size_t)c->nx * c->nz);
+    if (st != ZK_OK) return st;
+    c->net = net;
+    c->base_M = base_order;
+    set_scales(c, in_scale, out_scale);
+    c->check_every = check_every;
+    c->check_tol = check_tol;
+    c->closure_on = true;
+    c->nchecks = 0;
+    c->nsteps = 0;
+    c->fallback_step = -1;
+    c->last_err = -1.0;
+    drop_graph(c);
+    return ZK_OK;
+}
+
+zk_status zk_closure_status(const zk_ctx* c, int* active, int* checks, long long* fallback_step, double* last_err) {
+    if (!c) return ZK_EINVAL;
+    if (active) *active = c->closure_on ? 1 : 0;
+    if (checks) *checks = c->nchecks;
+    if (fallback_step) *fallback_step = c->fallback_step;
+    if (last_err) *last_err = c->last_err;
     return ZK_OK;
 }
 

@@ -426,4 +426,159 @@ col2_kernel(const ColArgs<T> a, const cx<T>* __restrict__ tw) {
     }
 }
 
+
+
+// ---------------------------------------------------------------------------
+// Learned closure: features in, residual out (compact spectra [nz][hx]).
+// ---------------------------------------------------------------------------
+struct ClosureScales { float in[6]; float out[2]; };
+
+// Six feature spectra at state (se, sp) with the low-order right-hand side
+// (de, dp): eta, i kx eta, i kz eta, G0 psi, de - G0 psi, dp + g eta, each
+// divided by its input scale; the z Nyquist row is zero.
+template <typename T>
+__global__ void closure_prep_kernel(const cx<T>* __restrict__ se, const cx<T>* __restrict__ sp,
+                                    const cx<T>* __restrict__ de, const cx<T>* __restrict__ dp, cx<T>* __restrict__ out,
+                                    int nz, int hx, T kx0, T kz0, T h, T g, ClosureScales sc) {
+    const long long n = (long long)nz * hx;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int ic = (int)(i / hx), col = (int)(i - (long long)ic * hx);
+        cx<T> v[6];
+        if (ic == nz / 2) {
+            for (int c = 0; c < 6; ++c) v[c] = mk<T>(0, 0);
+        } else {
+            const int mz = ic < nz / 2 ? ic : ic - nz;
+            const T kx = kx0 * (T)col, kz = kz0 * (T)mz;
+            const T k = d_sqrt(kx * kx + kz * kz);
+            const T G0 = k * tanh_kh(k * h);
+            const cx<T> e = se[i], p = sp[i];
+            const cx<T> g0p = cscale(p, G0);
+            v[0] = e;
+            v[1] = mk<T>(-kx * e.y, kx * e.x);
+            v[2] = mk<T>(-kz * e.y, kz * e.x);
+            v[3] = g0p;
+            v[4] = csub(de[i], g0p);
+            v[5] = cadd(dp[i], cscale(e, g));
+        }
+        for (int c = 0; c < 6; ++c) out[(long long)c * n + i] = cscale(v[c], (T)(1.0f / sc.in[c]));
+    }
+}
+
+// Corrected right-hand side (ko + out_scale T(k) R_hat, eta's k = 0 mode zero)
+// followed by the same epilogue as the final column kernel: FIN_RHS writes it
+// back to ko, FIN_RK1..4 combine the RK4 stages (filter of Eq. 17 at the last).
+template <typename T>
+__global__ void closure_combine_kernel(ColArgs<T> a, const cx<T>* __restrict__ Re, const cx<T>* __restrict__ Rp,
+                                       ClosureScales sc) {
+    const int NZ = a.nz_grid, hx = a.hx;
+    const long long n = (long long)NZ * hx;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int ic = (int)(idx / hx), col = (int)(idx - (long long)ic * hx);
+        if (ic == NZ / 2) {
+            if (a.mode == FIN_RHS) { a.ko_eta[idx] = mk<T>(0, 0); a.ko_psi[idx] = mk<T>(0, 0); }
+            continue;
+        }
+        const int mz = ic < NZ / 2 ? ic : ic - NZ;
+        const T kxc = a.kx0 * (T)col, kz = a.kz0 * (T)mz;
+        T tp = 1;
+        if (a.taper) {
+            const T kk2 = (kxc * kxc + kz * kz) / (a.kc * a.kc);
+            const T k4 = kk2 * kk2;
+            tp = d_exp(-(k4 * k4));
+        }
+        cx<T> de = cadd(a.ko_eta[idx], cscale(Re[idx], (T)sc.out[0] * tp));
+        const cx<T> dp = cadd(a.ko_psi[idx], cscale(Rp[idx], (T)sc.out[1] * tp));
+        if (col == 0 && mz == 0) de = mk<T>(0, 0);
+        switch (a.mode) {
+        case FIN_RHS:
+            a.ko_eta[idx] = de; a.ko_psi[idx] = dp;
+            break;
+        case FIN_RK1: {
+            a.ka_eta[idx] = de; a.ka_psi[idx] = dp;
+            const T hd = (T)0.5 * a.dt;
+            a.ys_eta[idx] = cadd(a.y_eta[idx], cscale(de, hd));
+            a.ys_psi[idx] = cadd(a.y_psi[idx], cscale(dp, hd));
+        } break;
+        case FIN_RK2:
+        case FIN_RK3: {
+            a.ka_eta[idx] = cadd(a.ka_eta[idx], cscale(de, (T)2));
+            a.ka_psi[idx] = cadd(a.ka_psi[idx], cscale(dp, (T)2));
+            const T hd = a.mode == FIN_RK2 ? (T)0.5 * a.dt : a.dt;
+            a.ys_eta[idx] = cadd(a.y_eta[idx], cscale(de, hd));
+            a.ys_psi[idx] = cadd(a.y_psi[idx], cscale(dp, hd));
+        } break;
+        case FIN_RK4: {
+            const T w = a.dt / (T)6;
+            T A = 1;
+            if (a.filter) {
+                const T rx = (T)col / (T)a.hx;
+                const T rz = (T)(mz < 0 ? -mz : mz) / (T)(NZ / 2);
+                A = (T)0.125 * ((T)5 + (T)4 * d_cospi(rx) - d_cospi((T)2 * rx)) *
+                    ((T)0.125 * ((T)5 + (T)4 * d_cospi(rz) - d_cospi((T)2 * rz)));
+            }
+            const cx<T> ye = cadd(a.y_eta[idx], cscale(cadd(a.ka_eta[idx], de), w));
+            const cx<T> yp = cadd(a.y_psi[idx], cscale(cadd(a.ka_psi[idx], dp), w));
+            a.y_eta[idx] = cscale(ye, A);
+            a.y_psi[idx] = cscale(yp, A);
+        } break;
+        default: break;
+        }
+    }
+}
+
+// out_c = (hi_c - lo_c) / scale_c for the two components (compact spectra).
+template <typename T>
+__global__ void closure_diff_kernel(const cx<T>* __restrict__ hi, const cx<T>* __restrict__ lo, cx<T>* __restrict__ out,
+                                    long long n, ClosureScales sc) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < 2 * n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = cscale(csub(hi[i], lo[i]), (T)(1.0f / sc.out[i < n ? 0 : 1]));
+}
+
+// Fallback check: with D = f_high - f_low (d = 6 .. 1 / 2) and the predicted
+// P = out_scale T(k) R_hat, FP64 sums of |D - P|^2 and |D|^2 over the half
+// spectrum (kx > 0 columns weighted 2) into part[2 * block].
+template <typename T>
+__global__ void closure_err_kernel(const cx<T>* __restrict__ fe, const cx<T>* __restrict__ fp,
+                                   const cx<T>* __restrict__ le, const cx<T>* __restrict__ lp,
+                                   const cx<T>* __restrict__ Re, const cx<T>* __restrict__ Rp, int nz, int hx, T kx0,
+                                   T kz0, T kc, int taper, ClosureScales sc, double* __restrict__ part) {
+    const long long n = (long long)nz * hx;
+    double num = 0.0, den = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int ic = (int)(i / hx), col = (int)(i - (long long)ic * hx);
+        if (ic == nz / 2) continue;
+        const int mz = ic < nz / 2 ? ic : ic - nz;
+        const T kx = kx0 * (T)col, kz = kz0 * (T)mz;
+        T tp = 1;
+        if (taper) {
+            const T kk2 = (kx * kx + kz * kz) / (kc * kc);
+            const T k4 = kk2 * kk2;
+            tp = d_exp(-(k4 * k4));
+        }
+        const double w = col == 0 ? 1.0 : 2.0;
+        const bool zero = col == 0 && mz == 0;
+        const cx<T> De = csub(fe[i], le[i]), Dp = csub(fp[i], lp[i]);
+        const cx<T> Pe = zero ? mk<T>(0, 0) : cscale(Re[i], (T)sc.out[0] * tp);
+        const cx<T> Pp = cscale(Rp[i], (T)sc.out[1] * tp);
+        const double ex = (double)De.x - Pe.x, ey = (double)De.y - Pe.y;
+        const double px = (double)Dp.x - Pp.x, py = (double)Dp.y - Pp.y;
+        num += w * (ex * ex + ey * ey + px * px + py * py);
+        den += w * ((double)De.x * De.x + (double)De.y * De.y + (double)Dp.x * Dp.x + (double)Dp.y * Dp.y);
+    }
+    __shared__ double red[2][32];
+    for (int o = 16; o > 0; o >>= 1) {
+        num += __shfl_down_sync(0xffffffffu, num, o);
+        den += __shfl_down_sync(0xffffffffu, den, o);
+    }
+    if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = num; red[1][threadIdx.x >> 5] = den; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += red[0][w]; b += red[1][w]; }
+        part[2 * blockIdx.x] = a;
+        part[2 * blockIdx.x + 1] = b;
+    }
+}
+
 }  // namespace zk

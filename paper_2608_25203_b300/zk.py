@@ -30,6 +30,9 @@ EXPORTS = [
     "zk_batch_create", "zk_batch_destroy", "zk_batch_set_options", "zk_batch_set_state", "zk_batch_get_state",
     "zk_batch_energy", "zk_batch_step", "zk_batch_sync", "zk_batch_info", "zk_batch_group", "zk_batch_set_shape",
     "zk_batch_autotune",
+    "zk_net_create", "zk_net_destroy", "zk_net_param_count", "zk_net_set_params", "zk_net_get_params",
+    "zk_net_forward", "zk_net_backward", "zk_net_adam", "zk_net_train_step",
+    "zk_closure_features", "zk_closure_set", "zk_closure_status",
     "zk_strerror", "zk_version",
 ]
 
@@ -93,6 +96,18 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "zk_batch_group": ([vp, i] + [ctypes.POINTER(i)] * 7, i),
         "zk_batch_set_shape": ([vp, i, i, i, i], i),
         "zk_batch_autotune": ([vp, d, ctypes.c_char_p, ctypes.POINTER(i), ctypes.POINTER(i)], i),
+        "zk_net_create": ([ctypes.POINTER(vp), i, i, i], i),
+        "zk_net_destroy": ([vp], None),
+        "zk_net_param_count": ([vp, ctypes.POINTER(i)], i),
+        "zk_net_set_params": ([vp, vp, i], i),
+        "zk_net_get_params": ([vp, vp, i], i),
+        "zk_net_forward": ([vp, vp, vp, i, i, i, vp], i),
+        "zk_net_backward": ([vp, vp, vp, vp, vp], i),
+        "zk_net_adam": ([vp, vp, d, vp], i),
+        "zk_net_train_step": ([vp, vp, vp, i, i, i, d, pd, vp], i),
+        "zk_closure_features": ([vp, i, vp, vp, vp, vp], i),
+        "zk_closure_set": ([vp, vp, i, vp, vp, i, d], i),
+        "zk_closure_status": ([vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(ctypes.c_longlong), pd], i),
         "zk_strerror": ([i], ctypes.c_char_p),
         "zk_version": ([], ctypes.c_char_p),
     }
@@ -465,3 +480,132 @@ class Batch:
 
     def autotune(self, dt, cache_path=None):
         return zk_batch_autotune(self.b, dt, cache_path)
+
+
+# ---- learned closure --------------------------------------------------------
+def _dptr(t):
+    """Device pointer of a contiguous float32 CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise ValueError("expected a contiguous float32 CUDA tensor")
+    return t.data_ptr()
+
+
+def _fvec(v, n):
+    if v is None:
+        return None
+    a = np.ascontiguousarray(np.asarray(v, dtype=np.float32).reshape(n))
+    return a
+
+
+def zk_net_create(cin=6, width=32, cout=2):
+    n = ctypes.c_void_p()
+    _check("zk_net_create", load().zk_net_create(ctypes.byref(n), cin, width, cout))
+    return n
+
+
+def zk_net_destroy(n):
+    load().zk_net_destroy(n)
+
+
+def zk_net_param_count(n):
+    c = ctypes.c_int()
+    _check("zk_net_param_count", load().zk_net_param_count(n, ctypes.byref(c)))
+    return c.value
+
+
+def zk_net_set_params(n, theta):
+    if isinstance(theta, np.ndarray):
+        a = np.ascontiguousarray(theta, dtype=np.float32)
+        _check("zk_net_set_params", load().zk_net_set_params(n, a.ctypes.data, 0))
+    else:
+        _check("zk_net_set_params", load().zk_net_set_params(n, _dptr(theta), 1))
+
+
+def zk_net_get_params(n):
+    a = np.empty(zk_net_param_count(n), np.float32)
+    _check("zk_net_get_params", load().zk_net_get_params(n, a.ctypes.data, 0))
+    return a
+
+
+def zk_net_forward(n, x, y=None, stream=None):
+    B, C, H, W = x.shape
+    _check("zk_net_forward", load().zk_net_forward(n, _dptr(x), _dptr(y), B, H, W, stream))
+
+
+def zk_net_backward(n, dy, grad=None, dx=None, stream=None):
+    _check("zk_net_backward", load().zk_net_backward(n, _dptr(dy), _dptr(grad), _dptr(dx), stream))
+
+
+def zk_net_adam(n, grad=None, lr=1e-3, stream=None):
+    _check("zk_net_adam", load().zk_net_adam(n, _dptr(grad), float(lr), stream))
+
+
+def zk_net_train_step(n, x, target, lr, stream=None, want_loss=True):
+    B, C, H, W = x.shape
+    loss = ctypes.c_double(float("nan"))
+    _check("zk_net_train_step", load().zk_net_train_step(n, _dptr(x), _dptr(target), B, H, W, float(lr),
+                                                         ctypes.byref(loss) if want_loss else None, stream))
+    return loss.value
+
+
+def zk_closure_features(ctx, base_order, feat, target=None, in_scale=None, out_scale=None):
+    a, b = _fvec(in_scale, 6), _fvec(out_scale, 2)
+    _check("zk_closure_features", load().zk_closure_features(
+        ctx, int(base_order), None if a is None else a.ctypes.data, None if b is None else b.ctypes.data,
+        _dptr(feat), _dptr(target)))
+
+
+def zk_closure_set(ctx, net, base_order=2, in_scale=None, out_scale=None, check_every=50, check_tol=0.2):
+    a, b = _fvec(in_scale, 6), _fvec(out_scale, 2)
+    _check("zk_closure_set", load().zk_closure_set(
+        ctx, net, int(base_order), None if a is None else a.ctypes.data, None if b is None else b.ctypes.data,
+        int(check_every), float(check_tol)))
+
+
+def zk_closure_status(ctx):
+    a, c, f, e = ctypes.c_int(), ctypes.c_int(), ctypes.c_longlong(), ctypes.c_double()
+    _check("zk_closure_status", load().zk_closure_status(ctx, ctypes.byref(a), ctypes.byref(c), ctypes.byref(f),
+                                                         ctypes.byref(e)))
+    return dict(active=a.value, checks=c.value, fallback_step=f.value, last_err=e.value)
+
+
+class Net:
+    """The closure network (6 -> 32 -> 32 -> 32 -> 2 periodic conv net) on the current CUDA device."""
+
+    def __init__(self, theta=None):
+        self.n = zk_net_create()
+        self.nparam = zk_net_param_count(self.n)
+        if theta is not None:
+            self.set_params(theta)
+
+    def close(self):
+        if self.n is not None:
+            zk_net_destroy(self.n)
+            self.n = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, theta):
+        zk_net_set_params(self.n, theta)
+
+    def params(self):
+        return zk_net_get_params(self.n)
+
+    def forward(self, x, y=None, stream=None):
+        zk_net_forward(self.n, x, y, stream)
+
+    def backward(self, dy, grad=None, dx=None, stream=None):
+        zk_net_backward(self.n, dy, grad, dx, stream)
+
+    def adam(self, grad=None, lr=1e-3, stream=None):
+        zk_net_adam(self.n, grad, lr, stream)
+
+    def train_step(self, x, target, lr, stream=None, want_loss=True):
+        return zk_net_train_step(self.n, x, target, lr, stream, want_loss)
