@@ -32,6 +32,16 @@ with ms per step for each case; the paper's RTX 4090 times are context only.
 tile (seeds 1000 + tile), eps = 0.5, RK4 dt = 0.02 s, 200 steps, FP32, all
 advanced by one graph per step. Timed with the default launch shapes and again
 after the autotuner; value = tile-steps/s after tuning.
+
+--workload closure: the learned closure. Training data from order-6 FP32 runs
+on 64 seeded 512^2 seas (L = 400 m, h = 30 m, Hs ~ U[1, 4], Tp ~ U[8, 12],
+seeds 100-163, eps = 0.5, a pair every 10 steps for 200 steps), network
+trained on the GPU by the library's kernels; evaluated at 1024^2 (L = 800 m)
+and 2048^2 (L = 1600 m) on seeds 7 and 8 (Hs = 3 m, Tp = 10 s) for 1000 RK4
+steps against plain order 6: steps/s and eta error of plain M = 2..6 and of
+M = 2 + network (with the order-6 fallback check every 50 steps at 0.2, and
+with the check off). value = plain-series cost at the closure's eta error
+(log-linear interpolation over M) / closure cost, at 2048^2.
 """
 from __future__ import annotations
 
@@ -280,6 +290,105 @@ def batch_arm(args):
     return 0
 
 
+def closure_arm(args):
+    """Train the closure network, then compare it with the plain series at 1024^2 and 2048^2."""
+    import numpy as np
+    import torch
+
+    from paper_2608_25203_b300 import closure_train as ct
+    from paper_2608_25203_b300 import seas
+    from paper_2608_25203_b300 import zk
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    stream = torch.cuda.current_stream()
+    eps, dt, h = 0.5, 0.02, 30.0
+    steps = args.frames or 1000
+    t0 = time.time()
+    X, T, kept = ct.make_dataset(list(range(100, 164)), n=512, L=400.0, h=h, eps=eps, snaps=20, every=10)
+    t_data = time.time() - t0
+    ins, outs = ct.channel_scales(X, T)
+    nv = 40
+    Xv, Tv = X[-nv:].clone(), T[-nv:].clone()
+    t0 = time.time()
+    net, losses = ct.train(X[:-nv], T[:-nv], ins, outs, iters=3000, batch=8, lr=1e-3, lr_end=1e-5, log_every=500)
+    torch.cuda.synchronize()
+    t_train = time.time() - t0
+    Xv /= torch.as_tensor(ins, device="cuda")[None, :, None, None]
+    Tv /= torch.as_tensor(outs, device="cuda")[None, :, None, None]
+    val = ct.validation_loss(net, Xv, Tv)
+    del X, T, Xv, Tv
+    torch.cuda.empty_cache()
+
+    def run(n, L, M, seed, closure=None):
+        eta, psi, _ = seas.jonswap_sea(n, n, L, L, h, 3.0, 10.0, seed)
+        s = zk.Zakharov(n, n, L, L, h, M=6 if closure else M, eps=eps, stream=stream.cuda_stream)
+        e32, p32 = eta.astype(np.float32), psi.astype(np.float32)
+
+        def start():
+            s.set_state(e32, p32)
+            if closure:
+                zk.zk_closure_set(s.ctx, net.n, 2, ins, outs, check_every=closure[0], check_tol=closure[1])
+
+        start()
+        s.step(dt, 3)                      # graph capture and warm-up, then restart
+        torch.cuda.synchronize()
+        start()
+        out, done, ms = {}, 0, 0.0
+        for chk in (100, 500, 1000):
+            if chk > steps:
+                break
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.step(dt, chk - done)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+            done = chk
+            out[chk] = s.get_state()[0]
+        st = zk.zk_closure_status(s.ctx) if closure else None
+        s.close()
+        return out, ms / done, st
+
+    results = {}
+    for n, L in ((1024, 800.0), (2048, 1600.0)):
+        per = {}
+        for seed in (7, 8):
+            ref, ms6, _ = run(n, L, 6, seed)
+            row = {"M6": {"ms": ms6, "err": {k: 0.0 for k in ref}}}
+            for M in (2, 3, 4, 5):
+                o, ms, _ = run(n, L, M, seed)
+                row[f"M{M}"] = {"ms": ms, "err": {k: float(np.linalg.norm(o[k] - ref[k]) / np.linalg.norm(ref[k])) for k in o}}
+            for name, cfg in (("M2+net", (50, 0.2)), ("M2+net_nocheck", (0, 1.0))):
+                o, ms, st = run(n, L, 2, seed, closure=cfg)
+                row[name] = {"ms": ms, "status": st,
+                             "err": {k: float(np.linalg.norm(o[k] - ref[k]) / np.linalg.norm(ref[k])) for k in o}}
+            per[seed] = row
+        last = max(per[7]["M6"]["err"])
+        # plain cost-error curve at the last step (mean over seeds), log-linear in the error
+        pts = []
+        for M in (2, 3, 4, 5):
+            pts.append((np.mean([per[s][f"M{M}"]["err"][last] for s in per]), np.mean([per[s][f"M{M}"]["ms"] for s in per])))
+        learned_err = float(np.mean([per[s]["M2+net_nocheck"]["err"][last] for s in per]))
+        learned_ms = float(np.mean([per[s]["M2+net_nocheck"]["ms"] for s in per]))
+        pts.sort()
+        le = np.log([p[0] for p in pts])
+        cost_at = float(np.interp(np.log(learned_err), le, [p[1] for p in pts]))
+        results[n] = {"seeds": per, "learned_err": learned_err, "learned_ms": learned_ms,
+                      "plain_ms_at_learned_err": cost_at, "ratio": cost_at / learned_ms}
+    print(json.dumps({
+        "metric": "learned closure: plain-series cost at equal eta error / closure cost (2048^2)",
+        "value": results[2048]["ratio"], "unit": "x", "higher_is_better": True, "steps": steps, "dtype": "f32",
+        "data": "synthetic", "n_gpus": 1,
+        "config": {"workload": "closure M=2 + 4-layer conv net (6-32-32-32-2) vs plain M=2..6; eval JONSWAP "
+                               "Hs=3 Tp=10 h=30, eps=0.5, RK4 dt=0.02, seeds 7, 8; train 512^2 seeds 100-163"},
+        "training": {"pairs": int(20 * len(kept)), "trajectories": len(kept), "data_s": t_data, "train_s": t_train,
+                     "iters": 3000, "batch": 8, "val_loss_scaled": val, "losses": losses,
+                     "in_scale": [float(x) for x in ins], "out_scale": [float(x) for x in outs]},
+        "results": results}), flush=True)
+    net.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -289,7 +398,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--profile-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="sea", choices=["sea", "tank", "batch"])
+    ap.add_argument("--workload", default="sea", choices=["sea", "tank", "batch", "closure"])
     ap.add_argument("--frames", type=int, default=None,
                     help="timed steps of --workload tank (default 2000 per case) or batch (default 200)")
     args = ap.parse_args()
@@ -297,6 +406,8 @@ def main():
         return tank_arm(args)
     if args.workload == "batch":
         return batch_arm(args)
+    if args.workload == "closure":
+        return closure_arm(args)
     if args.impl == "reference":
         return reference_arm(args)
     if args.warmup < 3:
