@@ -27,9 +27,10 @@ definition, restated by the CUDA kernels:
   through the network (rounding passed straight through), Adam (Kingma & Ba,
   2015) with bias correction.
 
-Parity unpinned: nothing in the paper fixes the trained network's values;
-every function below is pinned against definitions (brute-force sums, finite
-differences, closed-form Adam steps) by the CPU tests.
+The paper prints no learned component, so no pin comes from it; every
+function below is pinned against its definition (brute-force sums, finite
+differences, closed-form Adam steps, special cases of the features) by the
+CPU tests, and the trained parameters are this build's own output.
 """
 from __future__ import annotations
 
