@@ -42,6 +42,13 @@ steps against plain order 6: steps/s and eta error of plain M = 2..6 and of
 M = 2 + network (with the order-6 fallback check every 50 steps at 0.2, and
 with the check off). value = plain-series cost at the closure's eta error
 (log-linear interpolation over M) / closure cost, at 2048^2.
+
+--workload precision: the sea workload's sea at 1024^2 (L = 800 m, same dx)
+for 500 RK4 steps in FP64 (the reference; one right-hand side checked against
+the FP64 oracle at this size), FP32, and FP32 with FP64 series sums: eta and
+psi relative L2 against FP64, Hamiltonian difference, steps/s; and at 2048^2
+(the sea workload) the FP32 and FP32 + FP64-series throughput and their
+difference after 500 steps. value = FP32 eta error vs FP64 at 1024^2.
 """
 from __future__ import annotations
 
@@ -389,6 +396,77 @@ def closure_arm(args):
     return 0
 
 
+def precision_arm(args):
+    """FP32 / FP32 with FP64 series sums / FP64 on the sea workload's sea."""
+    import numpy as np
+    import torch
+
+    from oracle import Grid, Oracle
+    from paper_2608_25203_b300 import seas
+    from paper_2608_25203_b300 import zk
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    stream = torch.cuda.current_stream()
+    steps = args.frames or 500
+    dt, eps, M, h = W["dt"], W["eps"], W["M"], W["h"]
+
+    def run(n, L, prec, s64, nsteps):
+        eta, psi, _ = seas.jonswap_sea(n, n, L, L, h, W["Hs"], W["Tp"], W["seed"])
+        s = zk.Zakharov(n, n, L, L, h, W["g"], M, prec, eps=eps, stream=stream.cuda_stream)
+        if s64:
+            zk.zk_set_series_fp64(s.ctx, True)
+        e32, p32 = eta.astype(np.float32), psi.astype(np.float32)
+        s.set_state(e32, p32) if prec == zk.ZK_F32 else s.set_state(e32.astype(np.float64), p32.astype(np.float64))
+        s.step(dt, 3)
+        torch.cuda.synchronize()
+        s.set_state(e32, p32) if prec == zk.ZK_F32 else s.set_state(e32.astype(np.float64), p32.astype(np.float64))
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        s.step(dt, nsteps)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1) / nsteps
+        e, p = s.get_state()
+        H = s.energy()[0]
+        s.close()
+        return e, p, H, ms, (e32, p32)
+
+    out = {}
+    n, L = 1024, 800.0
+    ref_e, ref_p, ref_H, ms64, (e32, p32) = run(n, L, zk.ZK_F64, False, steps)
+    # the FP64 context against the FP64 oracle: one right-hand side at this size
+    o = Oracle(Grid(n, n, L, L, h), M, eps=eps)
+    t0 = time.time()
+    de, dp = o.rhs(o.spectrum(e32.astype(np.float64)), o.spectrum(p32.astype(np.float64)))
+    t_orc = time.time() - t0
+    s = zk.Zakharov(n, n, L, L, h, W["g"], M, zk.ZK_F64, eps=eps)
+    s.set_state(e32.astype(np.float64), p32.astype(np.float64))
+    ge, gp = s.rhs()
+    s.close()
+    orc = {"eta_rhs_rel": float(np.linalg.norm(ge - o.physical(de)) / np.linalg.norm(o.physical(de))),
+           "psi_rhs_rel": float(np.linalg.norm(gp - o.physical(dp)) / np.linalg.norm(o.physical(dp))),
+           "oracle_s": t_orc}
+    out["1024"] = {"fp64": {"ms": ms64, "H": ref_H}, "fp64_vs_oracle_one_rhs": orc}
+    for name, s64 in (("fp32", False), ("fp32_series64", True)):
+        e, p, H, ms, _ = run(n, L, zk.ZK_F32, s64, steps)
+        out["1024"][name] = {"ms": ms, "eta_rel": float(np.linalg.norm(e - ref_e) / np.linalg.norm(ref_e)),
+                             "psi_rel": float(np.linalg.norm(p - ref_p) / np.linalg.norm(ref_p)),
+                             "H_rel": abs(H - ref_H) / ref_H}
+    n, L = W["nx"], W["Lx"]
+    a = run(n, L, zk.ZK_F32, False, steps)
+    b = run(n, L, zk.ZK_F32, True, steps)
+    out["2048"] = {"fp32_ms": a[3], "fp32_series64_ms": b[3],
+                   "eta_rel_diff": float(np.linalg.norm(a[0] - b[0]) / np.linalg.norm(b[0])),
+                   "psi_rel_diff": float(np.linalg.norm(a[1] - b[1]) / np.linalg.norm(b[1])),
+                   "fp64": "not supported at 2048^2 (FP64 contexts up to 1024^2)"}
+    print(json.dumps({"metric": "precision study: eta rel L2 vs FP64 after %d RK4 steps (1024^2, M=5)" % steps,
+                      "value": out["1024"]["fp32"]["eta_rel"], "unit": "rel L2", "higher_is_better": False,
+                      "steps": steps, "dtype": "f32/f64", "data": "synthetic", "n_gpus": 1,
+                      "config": {"workload": WORKLOAD.replace("2048x2048, L=1600 m", "1024x1024 (L=800 m) and 2048x2048")},
+                      "results": out}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -398,7 +476,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--profile-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="sea", choices=["sea", "tank", "batch", "closure"])
+    ap.add_argument("--workload", default="sea", choices=["sea", "tank", "batch", "closure", "precision"])
     ap.add_argument("--frames", type=int, default=None,
                     help="timed steps of --workload tank (default 2000 per case) or batch (default 200)")
     args = ap.parse_args()
@@ -408,6 +486,8 @@ def main():
         return batch_arm(args)
     if args.workload == "closure":
         return closure_arm(args)
+    if args.workload == "precision":
+        return precision_arm(args)
     if args.impl == "reference":
         return reference_arm(args)
     if args.warmup < 3:

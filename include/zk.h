@@ -190,6 +190,14 @@ zk_status zk_dno_static(const float *eta, const float *psi, float *v, int nx, in
                         double Lx, double Lz, double h, double g, int M, double eps, int taper,
                         void *stream);
 
+/* Precision form for FP32 contexts: with on = 1 the series sums of the
+ * right-hand side run in FP64 - the Taylor sums in eta inside each order's W(m)
+ * and Phi(m) (Sec. 4.2 recursion), the accumulation of sum_m eps^m G_m over the
+ * orders (Eq. 9) and the assembly of G_nl, W and N_psi (Eqs. 10-11) - while the
+ * transforms and the stored fields stay FP32. on = 0 restores the FP32 sums.
+ * FP64 contexts ignore the call (ZK_OK). ZK_EINVAL for other values of on. */
+zk_status zk_set_series_fp64(zk_ctx *ctx, int on);
+
 /* ---- Batched tiles (many independent seas advanced together) ----
  *
  * A batch holds ntiles independent periodic tiles; tile t has grid

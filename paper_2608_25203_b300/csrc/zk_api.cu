@@ -106,6 +106,7 @@ struct zk_ctx {
     // choice (0 / 1 / 2 = half / default / double), row blocks per SM (0 = all resident)
     int plan_v = 0, col_ci = 1, row_occ = 0;
     int m_run = 0;                         // order of the right-hand side being enqueued (<= M)
+    bool series64 = false;                 // FP32 context: series sums and accumulator in FP64
     // learned closure (FP32): order-base_M right-hand side plus the network's residual
     zk_net* net = nullptr;
     bool closure_on = false;
@@ -190,7 +191,7 @@ void make_twiddles(int n, std::vector<cx<T>>& out) {
 // ---------------------------------------------------------------------------
 // Launch helpers dispatched on the compile-time line lengths.
 // ---------------------------------------------------------------------------
-template <typename T, int NPX, int V>
+template <typename T, int NPX, int V, typename TA = T>
 cudaError_t launch_row_t(const RowArgs<T>& a, const cx<T>* tw, int npz, cudaStream_t s) {
     constexpr int TL = IPlan<NPX, V>::TL;
     // narrow groups: one line per group, rounded to whole warps; wide groups:
@@ -201,7 +202,7 @@ cudaError_t launch_row_t(const RowArgs<T>& a, const cx<T>* tw, int npz, cudaStre
     const int threads = groups * TL;
     const size_t smem = (size_t)nl * line_stride(NPX) * sizeof(cx<T>);
     if (threads > 1024 || smem > (size_t)smem_optin()) return cudaErrorInvalidConfiguration;
-    const void* fn = (const void*)row2_kernel<T, NPX, V>;
+    const void* fn = (const void*)row2_kernel<T, NPX, V, TA>;
     cudaError_t e = ensure_smem(fn, smem);
     if (e != cudaSuccess) return e;
     RowArgs<T> b = a;
@@ -213,13 +214,26 @@ cudaError_t launch_row_t(const RowArgs<T>& a, const cx<T>* tw, int npz, cudaStre
     if (a.occ > 0) per_sm = std::min(per_sm, a.occ);
     const int nb = std::max(1, a.nb);
     const int gx = std::max(1, std::min(npz, (per_sm * sms + nb - 1) / nb));
-    row2_kernel<T, NPX, V><<<dim3(gx, nb), threads, smem, s>>>(b, tw);
+    row2_kernel<T, NPX, V, TA><<<dim3(gx, nb), threads, smem, s>>>(b, tw);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_row(int npx, int v, const RowArgs<T>& a, const cx<T>* tw, int npz, cudaStream_t s) {
     if constexpr (sizeof(T) == 4) {
+        if (a.acc64) {   // FP64 series sums: default plans only
+            switch (npx) {
+            case 24: return launch_row_t<T, 24, 0, double>(a, tw, npz, s);
+            case 48: return launch_row_t<T, 48, 0, double>(a, tw, npz, s);
+            case 96: return launch_row_t<T, 96, 0, double>(a, tw, npz, s);
+            case 192: return launch_row_t<T, 192, 0, double>(a, tw, npz, s);
+            case 384: return launch_row_t<T, 384, 0, double>(a, tw, npz, s);
+            case 768: return launch_row_t<T, 768, 0, double>(a, tw, npz, s);
+            case 1536: return launch_row_t<T, 1536, 0, double>(a, tw, npz, s);
+            case 3072: return launch_row_t<T, 3072, 0, double>(a, tw, npz, s);
+            default: return cudaErrorInvalidValue;
+            }
+        }
         if (v == 1) {
             switch (npx) {
             case 768: return launch_row_t<T, 768, 1>(a, tw, npz, s);
@@ -426,6 +440,7 @@ struct Pipe {
         a.tacc = c->tacc;
         a.nb = c->nb;
         a.occ = c->row_occ;
+        a.acc64 = (sizeof(T) == 4 && c->series64) ? 1 : 0;
         return a;
     }
 
@@ -1015,7 +1030,8 @@ zk_status ctx_create(zk_ctx** out, int nx, int nz, double Lx, double Lz, const d
     c->tcol = (long long)c->nfields * c->fstride;
     c->tacc = (long long)c->npz * c->npx;
     if (st == ZK_OK) st = dalloc(c, &c->col, (size_t)c->tcol * c->csz * nb);
-    if (st == ZK_OK) st = dalloc(c, &c->acc, (size_t)c->tacc * rsz * nb);
+    // 8 bytes per element in every precision, so FP32 contexts can switch on FP64 series sums
+    if (st == ZK_OK) st = dalloc(c, &c->acc, (size_t)c->tacc * 8 * nb);
     if (st == ZK_OK) st = dalloc(c, &c->stage, (size_t)2 * nx * nz * kIoElem);
     if (st == ZK_OK) st = dalloc(c, &c->tank, (size_t)2 * (nx / 2) * (nz / 2) * 8);
     c->npartial = c->hx * nb;              // at most one column-kernel block per column
@@ -1052,7 +1068,8 @@ void tile_view(const zk_ctx* g, int t, zk_ctx* v) {
     v->ko_eta = off(g->ko_eta, oc); v->ko_psi = off(g->ko_psi, oc);
     v->h_eta = off(g->h_eta, oc); v->h_psi = off(g->h_psi, oc);
     v->col = off(g->col, (size_t)t * g->tcol * g->csz);
-    v->acc = off(g->acc, (size_t)t * g->tacc * (g->prec == ZK_F32 ? 4 : 8));
+    v->acc = off(g->acc, (size_t)t * g->tacc * ((g->prec == ZK_F32 && !g->series64) ? 4 : 8));
+    v->series64 = g->series64;
     v->nfields = g->nfields;
     v->fstride = g->fstride;
     v->stage = g->stage; v->tank = g->tank;
@@ -1439,6 +1456,16 @@ zk_status zk_closure_set(zk_ctx* c, zk_net* net, int base_order, const float* in
     c->fallback_step = -1;
     c->last_err = -1.0;
     drop_graph(c);
+    return ZK_OK;
+}
+
+zk_status zk_set_series_fp64(zk_ctx* c, int on) {
+    if (!c || (on != 0 && on != 1)) return ZK_EINVAL;
+    if (c->prec != ZK_F32) return ZK_OK;   // FP64 contexts sum in FP64 already
+    if (c->series64 != (on == 1)) {
+        c->series64 = on == 1;
+        drop_graph(c);
+    }
     return ZK_OK;
 }
 

@@ -78,6 +78,7 @@ struct RowArgs {
     long long tcol, tacc;
     int nb;                  // tiles in the launch (host side: grid.y)
     int occ;                 // host side: resident blocks per SM to use (0 = all)
+    int acc64;               // host side: series sums in FP64 (FP32 contexts; acc holds doubles)
 };
 
 // ---------------------------------------------------------------------------

@@ -24,7 +24,11 @@ template <> __device__ __forceinline__ void d_sincos<double>(double x, double* s
 // ---------------------------------------------------------------------------
 // Row kernel: persistent over padded rows.
 // ---------------------------------------------------------------------------
-template <typename T, int NPX, int V = 0>
+// TA: type of the series sums (the in-round W / Phi sums, the accumulator
+// across orders and the final G_nl / Bernoulli assembly); T, or double for
+// FP32 contexts with FP64 series accumulation (the accumulator buffer then
+// holds doubles).
+template <typename T, int NPX, int V = 0, typename TA = T>
 __global__ void __launch_bounds__(1024) row2_kernel(const RowArgs<T> a, const cx<T>* __restrict__ tw) {
     using P = IPlan<NPX, V>;
     constexpr int TL = P::TL;
@@ -41,7 +45,7 @@ __global__ void __launch_bounds__(1024) row2_kernel(const RowArgs<T> a, const cx
     const T kx0 = a.kx0;
     constexpr int SUB1 = NPX / P::R1;
     const cx<T>* colbase = a.colbase + (long long)blockIdx.y * a.tcol;
-    T* acc = a.acc + (long long)blockIdx.y * a.tacc;
+    TA* acc = reinterpret_cast<TA*>(a.acc) + (long long)blockIdx.y * a.tacc;
     cx<T>* out0 = a.out0 + (long long)blockIdx.y * a.tcol;
     cx<T>* out1 = a.out1 ? a.out1 + (long long)blockIdx.y * a.tcol : nullptr;
 
@@ -82,53 +86,53 @@ __global__ void __launch_bounds__(1024) row2_kernel(const RowArgs<T> a, const cx
             const cx<T> v = lines[(s >> 1) * LS + pidx(p)];
             return (s & 1) ? v.y : v.x;
         };
-        T* accrow = acc + (long long)zp * NPX;
+        TA* accrow = acc + (long long)zp * NPX;
         for (int p = threadIdx.x; p < NPX; p += blockDim.x) {
             if (a.kind == 0) {
                 const int r = a.r;
-                const T eta = slot(a.s_eta, p);
-                T W = 0, Phi = 0, ep = 1;
+                const TA eta = slot(a.s_eta, p);
+                TA W = 0, Phi = 0, ep = 1;
                 for (int q = 1; q <= r; ++q) {
-                    const T eq = ep * eta / (T)q;
-                    const T F = slot(a.s_F0 + (r - q), p);
+                    const TA eq = ep * eta / (TA)q;
+                    const TA F = slot(a.s_F0 + (r - q), p);
                     W += ep * F;
                     Phi -= eq * F;
                     ep = eq;
                 }
                 if (r >= 2) {
-                    T coef = a.epsp[r - 1];
+                    TA coef = a.epsp[r - 1];
                     if (r - 1 <= a.M - 3) {
-                        const T ex = slot(a.s_etax, p), ez = slot(a.s_etaz, p);
-                        coef += a.epsp[r + 1] * (ex * ex + ez * ez);
+                        const TA ex = slot(a.s_etax, p), ez = slot(a.s_etaz, p);
+                        coef += (TA)a.epsp[r + 1] * (ex * ex + ez * ez);
                     }
-                    const T prev = (r == 2) ? (T)0 : accrow[p];
+                    const TA prev = (r == 2) ? (TA)0 : accrow[p];
                     accrow[p] = prev + coef * W;
                 }
-                lines[pidx(p)] = mk<T>(Phi, 0);
+                lines[pidx(p)] = mk<T>((T)Phi, 0);
             } else {
                 const int M = a.M;
-                const T eps = a.eps;
-                const T ex = slot(a.s_etax, p), ez = slot(a.s_etaz, p);
-                const T px = slot(a.s_psix, p), pz = slot(a.s_psiz, p);
-                const T g0 = slot(a.s_g0psi, p);
-                const T g2 = ex * ex + ez * ez;
-                const T d = ex * px + ez * pz;
-                const T q2 = px * px + pz * pz;
-                T Gnl = 0;
+                const TA eps = a.eps;
+                const TA ex = slot(a.s_etax, p), ez = slot(a.s_etaz, p);
+                const TA px = slot(a.s_psix, p), pz = slot(a.s_psiz, p);
+                const TA g0 = slot(a.s_g0psi, p);
+                const TA g2 = ex * ex + ez * ez;
+                const TA d = ex * px + ez * pz;
+                const TA q2 = px * px + pz * pz;
+                TA Gnl = 0;
                 if (M >= 2) {
-                    const T eta = slot(a.s_eta, p);
-                    T W = 0, ep = 1;
+                    const TA eta = slot(a.s_eta, p);
+                    TA W = 0, ep = 1;
                     for (int q = 1; q <= M; ++q) {
-                        W += ep * slot(a.s_F0 + (M - q), p);
-                        ep = ep * eta / (T)q;
+                        W += ep * (TA)slot(a.s_F0 + (M - q), p);
+                        ep = ep * eta / (TA)q;
                     }
-                    Gnl = a.epsp[M - 1] * W - eps * d;
-                    if (M >= 3) Gnl += accrow[p] + a.epsp[2] * g2 * g0;
+                    Gnl = (TA)a.epsp[M - 1] * W - eps * d;
+                    if (M >= 3) Gnl += accrow[p] + (TA)a.epsp[2] * g2 * g0;
                 }
-                const T den = (T)1 + a.epsp[2] * g2;
-                const T Wb = (g0 + Gnl + eps * d) / den;
-                const T Np = eps * ((T)-0.5 * q2 + (T)0.5 * den * Wb * Wb);
-                lines[pidx(p)] = mk<T>(Gnl, Np);
+                const TA den = (TA)1 + (TA)a.epsp[2] * g2;
+                const TA Wb = (g0 + Gnl + eps * d) / den;
+                const TA Np = eps * ((TA)-0.5 * q2 + (TA)0.5 * den * Wb * Wb);
+                lines[pidx(p)] = mk<T>((T)Gnl, (T)Np);
             }
         }
         __syncthreads();

@@ -26,7 +26,7 @@ EXPORTS = [
     "zk_create", "zk_destroy", "zk_set_options", "zk_get_options", "zk_set_state", "zk_get_state",
     "zk_rhs", "zk_dno", "zk_step", "zk_energy", "zk_sync", "zk_device_bytes",
     "zk_launches_per_step", "zk_profile_step", "zk_dno_static", "zk_dno_inverse", "zk_relax",
-    "zk_set_state_tank", "zk_get_state_tank",
+    "zk_set_state_tank", "zk_get_state_tank", "zk_set_series_fp64",
     "zk_batch_create", "zk_batch_destroy", "zk_batch_set_options", "zk_batch_set_state", "zk_batch_get_state",
     "zk_batch_energy", "zk_batch_step", "zk_batch_sync", "zk_batch_info", "zk_batch_group", "zk_batch_set_shape",
     "zk_batch_autotune",
@@ -83,6 +83,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "zk_set_state_tank": ([vp, vp, vp, i, i], i),
         "zk_get_state_tank": ([vp, vp, vp, i, i], i),
         "zk_relax": ([vp, vp, vp, i, i, d, i], i),
+        "zk_set_series_fp64": ([vp, i], i),
         "zk_batch_create": ([ctypes.POINTER(vp), i, ctypes.POINTER(i), ctypes.POINTER(i), pd, pd, pd, d,
                              ctypes.POINTER(i), i], i),
         "zk_batch_destroy": ([vp], None),
@@ -243,6 +244,10 @@ def zk_get_state_tank(ctx, eta, psi, dtype=None):
     pe, de = _ptr(eta, dt)
     pp, _ = _ptr(psi, dt)
     _check("zk_get_state_tank", load().zk_get_state_tank(ctx, pe, pp, dt, de))
+
+
+def zk_set_series_fp64(ctx, on=True):
+    _check("zk_set_series_fp64", load().zk_set_series_fp64(ctx, 1 if on else 0))
 
 
 def zk_dno_inverse(ctx, v, iters=8, dtype=None):
