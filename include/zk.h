@@ -289,6 +289,17 @@ zk_status zk_net_adam(zk_net *n, const float *grad, double lr, void *stream);
  * one Adam step; *loss (may be NULL) receives the loss before the update. */
 zk_status zk_net_train_step(zk_net *n, const float *x, const float *target, int batch, int nz, int nx, double lr,
                             double *loss, void *stream);
+/* Inference engine of the network (used by zk_net_predict and by an attached
+ * closure): mode 0 = the FP32 SIMT kernels above; mode 1 (the default) = 5th-generation
+ * tensor cores (tcgen05 MMAs with FP32 accumulators in TMEM; the same FP16
+ * rounding of weights and layer inputs, FP32 sums, so results agree with mode 0
+ * to summation order). ZK_EINVAL for other modes. */
+zk_status zk_net_set_inference(zk_net *n, int mode);
+/* y [2][nz][nx] = net(x [6][nz][nx]) for one sample with the current engine
+ * (device arrays; nz, nx multiples of 16). Synchronises the stream;
+ * ZK_ETIMEOUT if a tensor-core block gave up waiting for its MMAs (the output
+ * is then invalid). */
+zk_status zk_net_predict(zk_net *n, const float *x, float *y, int nz, int nx, void *stream);
 /* Training pair at the context's current state (FP32 contexts): feat [6][nz][nx]
  * = eta, d_x eta, d_z eta, G0 psi, (d eta/dt)_b - G0 psi, (d psi/dt)_b + g eta,
  * each divided by in_scale[c] (NULL: 1); target [2][nz][nx] (may be NULL) =

@@ -198,7 +198,7 @@ cudaError_t launch_row_t(const RowArgs<T>& a, const cx<T>* tw, int npz, cudaStre
     // at most 1024 threads, lines beyond that taken in waves
     int nl = a.nlines, groups;
     if constexpr (TL < 32) { constexpr int per = 32 / TL; nl = (nl + per - 1) / per * per; groups = nl; }
-    else groups = std::min(nl, 1024 / TL);
+    else groups = std::min(nl, std::max(1, kRowMaxThreads / TL));
     const int threads = groups * TL;
     const size_t smem = (size_t)nl * line_stride(NPX) * sizeof(cx<T>);
     if (threads > 1024 || smem > (size_t)smem_optin()) return cudaErrorInvalidConfiguration;

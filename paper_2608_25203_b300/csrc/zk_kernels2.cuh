@@ -28,8 +28,15 @@ template <> __device__ __forceinline__ void d_sincos<double>(double x, double* s
 // across orders and the final G_nl / Bernoulli assembly); T, or double for
 // FP32 contexts with FP64 series accumulation (the accumulator buffer then
 // holds doubles).
+// Largest row-kernel block: it bounds the registers a thread may use (the
+// line groups of a wider round take their lines in waves).
+#ifndef ZK_ROW_MAX_THREADS
+#define ZK_ROW_MAX_THREADS 1024
+#endif
+constexpr int kRowMaxThreads = ZK_ROW_MAX_THREADS;
+
 template <typename T, int NPX, int V = 0, typename TA = T>
-__global__ void __launch_bounds__(1024) row2_kernel(const RowArgs<T> a, const cx<T>* __restrict__ tw) {
+__global__ void __launch_bounds__(kRowMaxThreads) row2_kernel(const RowArgs<T> a, const cx<T>* __restrict__ tw) {
     using P = IPlan<NPX, V>;
     constexpr int TL = P::TL;
     constexpr int HX = NPX / 3;

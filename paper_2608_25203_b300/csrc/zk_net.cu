@@ -22,6 +22,7 @@
 
 #include "../../include/zk.h"
 #include "zk_net_internal.h"
+#include "zk_tc.cuh"
 
 namespace {
 
@@ -225,6 +226,23 @@ __global__ void prep_weights_kernel(const float* __restrict__ th, float* __restr
     wf[woff(l) + ((c * out_of(l) + o) * K + (K - 1 - p)) * K + (K - 1 - q)] = v;
 }
 
+// Tensor-core inference: the three 3x3 layers' FP16-rounded weights as the B
+// operands of zk_tc::conv3_tc_kernel (canonical K-major, k = tap * CINP + c,
+// zero for the padded input channels c >= CIN): layer 1 [32][144], layers 2-3 [32][288].
+constexpr int kTcK1 = 9 * 16, kTcK2 = 9 * 32;
+constexpr int kTcOff2 = kWidth * kTcK1, kTcOff3 = kTcOff2 + kWidth * kTcK2, kTcTotal = kTcOff3 + kWidth * kTcK2;
+
+__global__ void prep_canon_kernel(const float* __restrict__ th, __half* __restrict__ wc) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kTcTotal) return;
+    const int l = i < kTcOff2 ? 0 : (i < kTcOff3 ? 1 : 2);
+    const int e = i - (l == 0 ? 0 : (l == 1 ? kTcOff2 : kTcOff3));
+    const int K = l == 0 ? kTcK1 : kTcK2, CINP = K / 9, CI = in_of(l);
+    const int co = e / K, k = e - co * K, tap = k / CINP, c = k - tap * CINP;
+    const float v = c < CI ? r16(th[woff(l) + ((co * CI + c) * 3 + tap / 3) * 3 + tap % 3]) : 0.f;
+    wc[(i - e) + zk_tc::canon_off(co, k, K)] = __float2half_rn(v);
+}
+
 template <int CIN, int COUT, int KS, bool RIN, int EPI>
 cudaError_t conv_fwd(const float* x, const float* w, const float* bias, const float* aux, float* y, int B, int H,
                      int W, cudaStream_t s) {
@@ -273,6 +291,10 @@ struct zk_net {
     double* dpart = nullptr;  // loss partials [1024] + loss [1]
     const float* x = nullptr; // input of the last forward pass (caller memory)
     int B = 0, H = 0, W = 0;
+    int infer_mode = 1;       // inference on 0 = the FP32 SIMT kernels, 1 = tensor cores (default)
+    __half* wc = nullptr;     // canonical FP16 B operands of the tensor-core layers
+    __half *a16 = nullptr, *b16 = nullptr;   // NHWC FP16 activations [H][W][32] (inference)
+    int* err = nullptr;       // set by a tensor-core block whose MMA wait ran out
     std::vector<void*> bufs;  // activation-sized allocations (freed on growth)
 };
 
@@ -288,6 +310,7 @@ void free_bufs(zk_net* n) {
     for (void* p : n->bufs) cudaFree(p);
     n->bufs.clear();
     n->h1 = n->h2 = n->h3 = n->y = n->ga = n->gb = nullptr;
+    n->a16 = n->b16 = nullptr;
     n->part = nullptr;
     n->cap = 0;
     n->part_cap = 0;
@@ -298,8 +321,35 @@ bool shape_ok(int B, int H, int W) { return B >= 1 && H >= TS && W >= TS && H % 
 cudaError_t prepare(zk_net* n, cudaStream_t s) {
     if (n->prepared) return cudaSuccess;
     prep_weights_kernel<<<(kParams + 255) / 256, 256, 0, s>>>(n->theta, n->w16, n->wf);
+    prep_canon_kernel<<<(kTcTotal + 255) / 256, 256, 0, s>>>(n->theta, n->wc);
     n->prepared = true;
     return cudaGetLastError();
+}
+
+template <int CINP, int CIN, bool IN_F32, int OUT>
+cudaError_t tc_layer(const void* x, const __half* wc, const float* bias, const float* w4, const float* b4, void* out,
+                     int H, int W, int* err, cudaStream_t s) {
+    constexpr int smem = zk_tc::conv_smem_bytes<CINP>();
+    auto fn = zk_tc::conv3_tc_kernel<CINP, CIN, IN_F32, OUT>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    fn<<<dim3(W / zk_tc::kTileW, H / zk_tc::kTileH), zk_tc::kTilePx, smem, s>>>(x, wc, bias, w4, b4, out, H, W, err);
+    return cudaGetLastError();
+}
+
+// Inference of one sample on the tensor cores: layer 1 from the FP32 features,
+// layers 2 and 3 through NHWC FP16 activations, layer 4 in layer 3's epilogue.
+cudaError_t tc_forward(zk_net* n, const float* x, int H, int W, cudaStream_t s) {
+    cudaError_t e = prepare(n, s);
+    const float* th = n->theta;
+    if (e == cudaSuccess)
+        e = tc_layer<16, kCin, true, 0>(x, n->wc, th + boff(0), nullptr, nullptr, n->a16, H, W, n->err, s);
+    if (e == cudaSuccess)
+        e = tc_layer<32, kWidth, false, 0>(n->a16, n->wc + kTcOff2, th + boff(1), nullptr, nullptr, n->b16, H, W, n->err, s);
+    if (e == cudaSuccess)
+        e = tc_layer<32, kWidth, false, 1>(n->b16, n->wc + kTcOff3, th + boff(2), n->w16 + woff(3), th + boff(3), n->y,
+                                           H, W, n->err, s);
+    return e;
 }
 
 cudaError_t forward(zk_net* n, const float* x, int B, int H, int W, cudaStream_t s) {
@@ -349,6 +399,13 @@ zk_status zk_net_reserve(zk_net* n, size_t pixels) {
         n->bufs.push_back(p);
         *act[i] = (float*)p;
     }
+    for (__half** q : {&n->a16, &n->b16}) {
+        void* p = nullptr;
+        zk_status st = net_alloc(&p, pixels * kWidth * sizeof(__half));
+        if (st != ZK_OK) { free_bufs(n); return st; }
+        n->bufs.push_back(p);
+        *q = (__half*)p;
+    }
     // weight-gradient partials: one row per 16 x 16 tile of the largest layer
     const size_t rows = pixels / (TS * TS) + 1;
     const size_t per = (size_t)kWidth * kWidth * 9 + kWidth;
@@ -365,6 +422,7 @@ zk_status zk_net_reserve(zk_net* n, size_t pixels) {
 cudaError_t zk_net_infer(zk_net* n, const float* x, const float** y, int B, int H, int W, cudaStream_t s) {
     if (!n || !y || !shape_ok(B, H, W) || (size_t)B * H * W > n->cap) return cudaErrorInvalidValue;
     *y = n->y;
+    if (n->infer_mode == 1 && B == 1) return tc_forward(n, x, H, W, s);
     return forward(n, x, B, H, W, s);
 }
 
@@ -373,7 +431,7 @@ extern "C" {
 void zk_net_destroy(zk_net* n) {
     if (!n) return;
     free_bufs(n);
-    void* p[7] = {n->theta, n->m, n->v, n->grad, n->w16, n->wf, n->dpart};
+    void* p[9] = {n->theta, n->m, n->v, n->grad, n->w16, n->wf, n->dpart, n->wc, n->err};
     for (void* q : p) if (q) cudaFree(q);
     delete n;
 }
@@ -396,9 +454,41 @@ zk_status zk_net_create(zk_net** out, int cin, int width, int cout) {
         st = net_alloc(&q, 1025 * sizeof(double));
         n->dpart = (double*)q;
     }
+    if (st == ZK_OK) {
+        void* q = nullptr;
+        st = net_alloc(&q, kTcTotal * sizeof(__half));
+        n->wc = (__half*)q;
+    }
+    if (st == ZK_OK) {
+        void* q = nullptr;
+        st = net_alloc(&q, sizeof(int));
+        n->err = (int*)q;
+    }
     if (st != ZK_OK) { zk_net_destroy(n); return st; }
     *out = n;
     return ZK_OK;
+}
+
+zk_status zk_net_set_inference(zk_net* n, int mode) {
+    if (!n || (mode != 0 && mode != 1)) return ZK_EINVAL;
+    n->infer_mode = mode;
+    return ZK_OK;
+}
+
+zk_status zk_net_predict(zk_net* n, const float* x, float* y, int nz, int nx, void* stream) {
+    if (!n || !x || !y || !shape_ok(1, nz, nx)) return ZK_EINVAL;
+    zk_status st = zk_net_reserve(n, (size_t)nz * nx);
+    if (st != ZK_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const float* out = nullptr;
+    if (cudaMemsetAsync(n->err, 0, sizeof(int), s) != cudaSuccess) return ZK_ECUDA;
+    cudaError_t e = zk_net_infer(n, x, &out, 1, nz, nx, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(y, out, (size_t)kCout * nz * nx * sizeof(float), cudaMemcpyDeviceToDevice, s);
+    int herr = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, n->err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return ZK_ECUDA;
+    return herr ? ZK_ETIMEOUT : ZK_OK;
 }
 
 zk_status zk_net_param_count(const zk_net* n, int* count) {

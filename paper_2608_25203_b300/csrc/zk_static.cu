@@ -123,7 +123,7 @@ cudaError_t s_row(const RowArgs<float>& a, const cx<float>* tw, int npz, cudaStr
     constexpr int TL = IPlan<NPX>::TL;
     int nl = a.nlines, groups;
     if constexpr (TL < 32) { constexpr int per = 32 / TL; nl = (nl + per - 1) / per * per; groups = nl; }
-    else groups = std::min(nl, 1024 / TL);
+    else groups = std::min(nl, kRowMaxThreads / TL);
     const size_t smem = (size_t)nl * line_stride(NPX) * sizeof(cx<float>);
     cudaError_t e = smem_attr((const void*)row2_kernel<float, NPX>, smem);
     if (e != cudaSuccess) return e;

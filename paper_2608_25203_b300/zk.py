@@ -31,7 +31,8 @@ EXPORTS = [
     "zk_batch_energy", "zk_batch_step", "zk_batch_sync", "zk_batch_info", "zk_batch_group", "zk_batch_set_shape",
     "zk_batch_autotune",
     "zk_net_create", "zk_net_destroy", "zk_net_param_count", "zk_net_set_params", "zk_net_get_params",
-    "zk_net_forward", "zk_net_backward", "zk_net_adam", "zk_net_train_step",
+    "zk_net_forward", "zk_net_backward", "zk_net_adam", "zk_net_train_step", "zk_net_set_inference",
+    "zk_net_predict",
     "zk_closure_features", "zk_closure_set", "zk_closure_status",
     "zk_strerror", "zk_version",
 ]
@@ -106,6 +107,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "zk_net_backward": ([vp, vp, vp, vp, vp], i),
         "zk_net_adam": ([vp, vp, d, vp], i),
         "zk_net_train_step": ([vp, vp, vp, i, i, i, d, pd, vp], i),
+        "zk_net_set_inference": ([vp, i], i),
+        "zk_net_predict": ([vp, vp, vp, i, i, vp], i),
         "zk_closure_features": ([vp, i, vp, vp, vp, vp], i),
         "zk_closure_set": ([vp, vp, i, vp, vp, i, d], i),
         "zk_closure_status": ([vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(ctypes.c_longlong), pd], i),
@@ -556,6 +559,15 @@ def zk_net_train_step(n, x, target, lr, stream=None, want_loss=True):
     return loss.value
 
 
+def zk_net_set_inference(n, mode):
+    _check("zk_net_set_inference", load().zk_net_set_inference(n, int(mode)))
+
+
+def zk_net_predict(n, x, y, stream=None):
+    C, H, W = x.shape[-3:]
+    _check("zk_net_predict", load().zk_net_predict(n, _dptr(x), _dptr(y), H, W, stream))
+
+
 def zk_closure_features(ctx, base_order, feat, target=None, in_scale=None, out_scale=None):
     a, b = _fvec(in_scale, 6), _fvec(out_scale, 2)
     _check("zk_closure_features", load().zk_closure_features(
@@ -614,3 +626,9 @@ class Net:
 
     def train_step(self, x, target, lr, stream=None, want_loss=True):
         return zk_net_train_step(self.n, x, target, lr, stream, want_loss)
+
+    def set_inference(self, mode):
+        zk_net_set_inference(self.n, mode)
+
+    def predict(self, x, y, stream=None):
+        zk_net_predict(self.n, x, y, stream)
