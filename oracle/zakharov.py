@@ -24,7 +24,10 @@ states the steps:
 * the Bernoulli right-hand side with eps (Eqs. 10-11).
 * 3/2-rule de-aliasing (Sec. 6.1): fields go to the (3nz/2, 3nx/2) grid by
   zero padding, products are formed there, results are truncated back at each
-  forward transform (reading: one padded grid per right-hand side).
+  forward transform (reading: one padded grid per right-hand side). Grid(pad=3)
+  pads to (3nz, 3nx) instead: the de-aliasing tailored to the higher-order
+  terms that Sec. 9 names as future work; every product of the series up to
+  order 5 (at most five band-limited factors) is then exact.
 * taper exp[-(|k|/kc)^8], kc = (2/3) kNyq, on every forward-transformed
   nonlinear quantity (Sec. 6.1; reading: kNyq = pi / max(dx, dz)).
 * (d eta/dt)_{k=0} := 0 (reading: every G_j has zero mean).
@@ -51,22 +54,27 @@ def mode_index(n: int) -> np.ndarray:
     return np.where(j < (n + 1) // 2, j, j - n)
 
 
-def padded_size(n: int) -> int:
-    """3/2-rule padded length (Sec. 6.1); an axis of length 1 stays 1."""
+def padded_size(n: int, pad: float = 1.5) -> int:
+    """Padded length pad * n: pad 1.5 is the 3/2 rule of Sec. 6.1; pad 3 makes
+    every product of up to five band-limited factors exact (no mode of such a
+    product folds back into the kept band). An axis of length 1 stays 1."""
     if n == 1:
         return 1
     if n % 2:
         raise ValueError("grid sizes must be even (or 1)")
-    return 3 * n // 2
+    if pad not in (1.5, 3.0, 4.5):
+        raise ValueError("pad must be 1.5, 3 or 4.5")
+    return int(round(pad * n))
 
 
 class Grid:
     """Doubly periodic grid [nz][nx] (x fastest) over depth h, gravity g."""
 
-    def __init__(self, nx: int, nz: int, Lx: float, Lz: float, h: float, g: float = 9.81):
+    def __init__(self, nx: int, nz: int, Lx: float, Lz: float, h: float, g: float = 9.81, pad: float = 1.5):
         self.nx, self.nz, self.Lx, self.Lz, self.h, self.g = nx, nz, float(Lx), float(Lz), float(h), float(g)
         self.dx, self.dz = self.Lx / nx, self.Lz / nz
-        self.npx, self.npz = padded_size(nx), padded_size(nz)
+        self.pad = pad
+        self.npx, self.npz = padded_size(nx, pad), padded_size(nz, pad)
         mx, mz = mode_index(nx), mode_index(nz)
         self.MZ, self.MX = np.meshgrid(mz, mx, indexing="ij")
         self.KX = 2 * np.pi * self.MX / self.Lx
