@@ -70,6 +70,20 @@ typedef struct {
 zk_status zk_create(zk_ctx **out, int nx, int nz, double Lx, double Lz,
                     double h, double g, int M, int precision);
 
+/* zk_create with a choice of padded grid for the nonlinear products:
+ * ZK_PAD_3_2 is the 3/2 rule of Sec. 6.1 (what zk_create uses): exact for
+ * quadratic products only. ZK_PAD_3 pads to 3 nx x 3 nz, which makes every
+ * product of up to five band-limited factors exact - all products of the
+ * order-M series for M <= 5 - the de-aliasing fitted to the higher-order terms
+ * that Sec. 9 lists as future work (the Bernoulli term, a quotient, stays
+ * approximate). ZK_PAD_3 costs about 4x the transform work and needs FP32
+ * and nx, nz <= 1024 (ZK_EUNSUPPORTED otherwise; series sums stay FP32).
+ * Other values of pad: ZK_EINVAL. */
+#define ZK_PAD_3_2 0
+#define ZK_PAD_3 1
+zk_status zk_create_ex(zk_ctx **out, int nx, int nz, double Lx, double Lz,
+                       double h, double g, int M, int precision, int pad);
+
 /* Release every device buffer and the context (NULL is accepted). */
 void zk_destroy(zk_ctx *ctx);
 
@@ -197,6 +211,22 @@ zk_status zk_dno_static(const float *eta, const float *psi, float *v, int nx, in
  * transforms and the stored fields stay FP32. on = 0 restores the FP32 sums.
  * FP64 contexts ignore the call (ZK_OK). ZK_EINVAL for other values of on. */
 zk_status zk_set_series_fp64(zk_ctx *ctx, int on);
+
+/* Adaptive order (the adaptive-order scheme Sec. 9 lists as future work, in
+ * its global form): the context keeps its order M as the maximum. Every
+ * check_every steps, before the step, it evaluates the order-M right-hand side
+ * f_M at the current state and then f_m for m = m_min, m_min + 1, ... and
+ * steps at the first m with |f_m - f_M| <= tol |f_M| (L2 over both spectra,
+ * FP64 sums), or at M if none qualifies. zk_rhs, zk_dno and zk_energy use the
+ * chosen order too. Checks synchronise the stream and cost up to
+ * M - m_min + 1 right-hand sides. check_every = 0 switches it off (order M
+ * again). ZK_EINVAL for m_min outside [1, M] or tol < 0; ZK_EUNSUPPORTED while
+ * a closure is attached. */
+zk_status zk_set_adaptive_order(zk_ctx *ctx, int m_min, double tol, int check_every);
+/* order: the order in use; checks made; err[m-1] (ZK_MAX_ORDER entries): the
+ * relative difference measured for order m at the last check (0 for M, -1 when
+ * not evaluated). */
+zk_status zk_adaptive_status(const zk_ctx *ctx, int *order, int *checks, double *err);
 
 /* ---- Batched tiles (many independent seas advanced together) ----
  *

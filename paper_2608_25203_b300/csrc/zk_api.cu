@@ -107,6 +107,7 @@ struct zk_ctx {
     int plan_v = 0, col_ci = 1, row_occ = 0;
     int m_run = 0;                         // order of the right-hand side being enqueued (<= M)
     bool series64 = false;                 // FP32 context: series sums and accumulator in FP64
+    bool pad3 = false;                     // padded grid 3N (exact series products) instead of 3N/2
     // learned closure (FP32): order-base_M right-hand side plus the network's residual
     zk_net* net = nullptr;
     bool closure_on = false;
@@ -123,6 +124,11 @@ struct zk_ctx {
     void* rbuf = nullptr;                  // [2][nz][nx] FP32 network output
     void* chk = nullptr;                   // 2 compact spectra: the high-order right-hand side
     double* cpart = nullptr;               // check partial sums
+    // adaptive order: every adapt_every steps pick the smallest order in
+    // [adapt_min, M] whose right-hand side is within adapt_tol of order M's
+    int adapt_every = 0, adapt_min = 1, adapt_checks = 0;
+    double adapt_tol = 0.0;
+    double adapt_err[ZK_MAX_ORDER + 1] = {};
     void *y_eta = nullptr, *y_psi = nullptr, *ys_eta = nullptr, *ys_psi = nullptr;
     void *ka_eta = nullptr, *ka_psi = nullptr, *ko_eta = nullptr, *ko_psi = nullptr;
     void *h_eta = nullptr, *h_psi = nullptr;   // IF-AB2 forcing history
@@ -191,7 +197,7 @@ void make_twiddles(int n, std::vector<cx<T>>& out) {
 // ---------------------------------------------------------------------------
 // Launch helpers dispatched on the compile-time line lengths.
 // ---------------------------------------------------------------------------
-template <typename T, int NPX, int V, typename TA = T>
+template <typename T, int NPX, int V, typename TA = T, int DIV = 3>
 cudaError_t launch_row_t(const RowArgs<T>& a, const cx<T>* tw, int npz, cudaStream_t s) {
     constexpr int TL = IPlan<NPX, V>::TL;
     // narrow groups: one line per group, rounded to whole warps; wide groups:
@@ -202,7 +208,7 @@ cudaError_t launch_row_t(const RowArgs<T>& a, const cx<T>* tw, int npz, cudaStre
     const int threads = groups * TL;
     const size_t smem = (size_t)nl * line_stride(NPX) * sizeof(cx<T>);
     if (threads > 1024 || smem > (size_t)smem_optin()) return cudaErrorInvalidConfiguration;
-    const void* fn = (const void*)row2_kernel<T, NPX, V, TA>;
+    const void* fn = (const void*)row2_kernel<T, NPX, V, TA, DIV>;
     cudaError_t e = ensure_smem(fn, smem);
     if (e != cudaSuccess) return e;
     RowArgs<T> b = a;
@@ -214,13 +220,25 @@ cudaError_t launch_row_t(const RowArgs<T>& a, const cx<T>* tw, int npz, cudaStre
     if (a.occ > 0) per_sm = std::min(per_sm, a.occ);
     const int nb = std::max(1, a.nb);
     const int gx = std::max(1, std::min(npz, (per_sm * sms + nb - 1) / nb));
-    row2_kernel<T, NPX, V, TA><<<dim3(gx, nb), threads, smem, s>>>(b, tw);
+    row2_kernel<T, NPX, V, TA, DIV><<<dim3(gx, nb), threads, smem, s>>>(b, tw);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_row(int npx, int v, const RowArgs<T>& a, const cx<T>* tw, int npz, cudaStream_t s) {
     if constexpr (sizeof(T) == 4) {
+        if (a.pad3) {    // 3N padding: FP32, default plans and sums
+            switch (npx) {
+            case 48: return launch_row_t<T, 48, 0, T, 6>(a, tw, npz, s);
+            case 96: return launch_row_t<T, 96, 0, T, 6>(a, tw, npz, s);
+            case 192: return launch_row_t<T, 192, 0, T, 6>(a, tw, npz, s);
+            case 384: return launch_row_t<T, 384, 0, T, 6>(a, tw, npz, s);
+            case 768: return launch_row_t<T, 768, 0, T, 6>(a, tw, npz, s);
+            case 1536: return launch_row_t<T, 1536, 0, T, 6>(a, tw, npz, s);
+            case 3072: return launch_row_t<T, 3072, 0, T, 6>(a, tw, npz, s);
+            default: return cudaErrorInvalidValue;
+            }
+        }
         if (a.acc64) {   // FP64 series sums: default plans only
             switch (npx) {
             case 24: return launch_row_t<T, 24, 0, double>(a, tw, npz, s);
@@ -256,10 +274,10 @@ cudaError_t launch_row(int npx, int v, const RowArgs<T>& a, const cx<T>* tw, int
     }
 }
 
-template <typename T, int NPZ, int CB, int V>
+template <typename T, int NPZ, int CB, int V, int DIV = 3>
 cudaError_t launch_col_t(const ColArgs<T>& a, const cx<T>* tw, cudaStream_t s, int* nblocks) {
     constexpr int TL = IPlan<NPZ, V>::TL;
-    constexpr int NZ = 2 * NPZ / 3;
+    constexpr int NZ = 2 * NPZ / DIV;
     constexpr int LS = line_stride(NPZ);
     const int threads = CB * TL < 32 ? 32 : CB * TL;
     const int groups = threads / TL;
@@ -268,9 +286,9 @@ cudaError_t launch_col_t(const ColArgs<T>& a, const cx<T>* tw, cudaStream_t s, i
     if (threads > 1024 || smem > (size_t)smem_optin()) return cudaErrorInvalidConfiguration;
     const int grid = (a.hx + CB - 1) / CB;
     if (nblocks) *nblocks = grid;
-    cudaError_t e = ensure_smem((const void*)col2_kernel<T, NPZ, CB, V>, smem);
+    cudaError_t e = ensure_smem((const void*)col2_kernel<T, NPZ, CB, V, DIV>, smem);
     if (e != cudaSuccess) return e;
-    col2_kernel<T, NPZ, CB, V><<<dim3(grid, std::max(1, a.nb)), threads, smem, s>>>(a, tw);
+    col2_kernel<T, NPZ, CB, V, DIV><<<dim3(grid, std::max(1, a.nb)), threads, smem, s>>>(a, tw);
     return cudaGetLastError();
 }
 
@@ -290,6 +308,19 @@ template <typename T>
 cudaError_t launch_col(int npz, int v, int ci, const ColArgs<T>& a, const cx<T>* tw, cudaStream_t s,
                        int* nblocks = nullptr) {
     if constexpr (sizeof(T) == 4) {
+        if (a.pad3) {    // 3N padding: FP32, default plans and blocking
+            constexpr int ES = (int)sizeof(cx<T>);
+            switch (npz) {
+            case 48: return launch_col_t<T, 48, col_cb<48, ES>(), 0, 6>(a, tw, s, nblocks);
+            case 96: return launch_col_t<T, 96, col_cb<96, ES>(), 0, 6>(a, tw, s, nblocks);
+            case 192: return launch_col_t<T, 192, col_cb<192, ES>(), 0, 6>(a, tw, s, nblocks);
+            case 384: return launch_col_t<T, 384, col_cb<384, ES>(), 0, 6>(a, tw, s, nblocks);
+            case 768: return launch_col_t<T, 768, col_cb<768, ES>(), 0, 6>(a, tw, s, nblocks);
+            case 1536: return launch_col_t<T, 1536, col_cb<1536, ES>(), 0, 6>(a, tw, s, nblocks);
+            case 3072: return launch_col_t<T, 3072, col_cb<3072, ES>(), 0, 6>(a, tw, s, nblocks);
+            default: return cudaErrorInvalidValue;
+            }
+        }
         if (v == 1) {
             switch (npz) {
             case 768: return launch_col_v<T, 768, 1>(ci, a, tw, s, nblocks);
@@ -420,6 +451,7 @@ struct Pipe {
         a.tst = c->tst;
         a.hb = reinterpret_cast<const T*>(c->hb);
         a.nb = c->nb;
+        a.pad3 = c->pad3 ? 1 : 0;
         return a;
     }
 
@@ -441,6 +473,7 @@ struct Pipe {
         a.nb = c->nb;
         a.occ = c->row_occ;
         a.acc64 = (sizeof(T) == 4 && c->series64) ? 1 : 0;
+        a.pad3 = c->pad3 ? 1 : 0;
         return a;
     }
 
@@ -701,6 +734,51 @@ struct Pipe {
         if (!(err <= c->check_tol)) {
             c->closure_on = false;
             c->fallback_step = c->nsteps;
+            drop_graph(c);
+        }
+        return ZK_OK;
+    }
+
+    // Adaptive order: f_M at the current state, then f_m for m = adapt_min, ...
+    // until |f_m - f_M| <= adapt_tol |f_M| (FP64 norms over the spectrum); the
+    // context then steps at that order (M if none is within the tolerance).
+    static zk_status adapt_check(zk_ctx* c, cudaStream_t s) {
+        const long long n = (long long)c->nz * c->hx;
+        const size_t compact = (size_t)n * sizeof(cx<T>);
+        ColArgs<T> r = col_base(c);
+        r.mode = FIN_RHS;
+        r.ko_eta = C(c->ko_eta);
+        r.ko_psi = C(c->ko_psi);
+        const int before = c->m_run;
+        c->m_run = c->M;
+        cudaError_t e = rhs(c, C(c->y_eta), C(c->y_psi), r, s, nullptr);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(c->chk, c->ko_eta, compact, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync((char*)c->chk + compact, c->ko_psi, compact, cudaMemcpyDeviceToDevice, s);
+        int chosen = c->M;
+        for (int m = 0; m <= ZK_MAX_ORDER; ++m) c->adapt_err[m] = -1.0;
+        c->adapt_err[c->M] = 0.0;
+        constexpr int nb = 256;
+        std::vector<double> hp(2 * nb);
+        for (int m = c->adapt_min; m < c->M && e == cudaSuccess; ++m) {
+            c->m_run = m;
+            e = rhs(c, C(c->y_eta), C(c->y_psi), r, s, nullptr);
+            if (e != cudaSuccess) break;
+            diff_norm_kernel<T><<<nb, 256, 0, s>>>(C(c->chk), C(c->chk) + n, C(c->ko_eta), C(c->ko_psi), c->nz, c->hx,
+                                                   c->cpart);
+            e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaMemcpyAsync(hp.data(), c->cpart, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) break;
+            double num = 0.0, den = 0.0;
+            for (int i = 0; i < nb; ++i) { num += hp[2 * i]; den += hp[2 * i + 1]; }
+            c->adapt_err[m] = den > 0.0 ? std::sqrt(num / den) : 0.0;
+            if (c->adapt_err[m] <= c->adapt_tol) { chosen = m; break; }
+        }
+        c->m_run = before;
+        if (e != cudaSuccess) return ZK_ECUDA;
+        ++c->adapt_checks;
+        if (chosen != before) {
+            c->m_run = chosen;
             drop_graph(c);
         }
         return ZK_OK;
@@ -998,7 +1076,7 @@ namespace {
 
 // One context over nb tiles of the same grid and order with depths h[0..nb-1].
 zk_status ctx_create(zk_ctx** out, int nx, int nz, double Lx, double Lz, const double* h, int nb, double g, int M,
-                     int precision) {
+                     int precision, int pad3 = 0) {
     if (!out || !h || nb < 1) return ZK_EINVAL;
     *out = nullptr;
     if (!is_pow2(nx) || !is_pow2(nz) || nx < 16 || nz < 16) return ZK_EINVAL;
@@ -1010,7 +1088,11 @@ zk_status ctx_create(zk_ctx** out, int nx, int nz, double Lx, double Lz, const d
     if (precision != ZK_F32 && precision != ZK_F64) return ZK_EINVAL;
     zk_ctx* c = new (std::nothrow) zk_ctx();
     if (!c) return ZK_ENOMEM;
-    c->nx = nx; c->nz = nz; c->npx = 3 * nx / 2; c->npz = 3 * nz / 2; c->hx = nx / 2;
+    if (pad3 && (precision != ZK_F32 || nx > 1024 || nz > 1024)) { delete c; return ZK_EUNSUPPORTED; }
+    c->pad3 = pad3 != 0;
+    c->nx = nx; c->nz = nz; c->hx = nx / 2;
+    c->npx = pad3 ? 3 * nx : 3 * nx / 2;
+    c->npz = pad3 ? 3 * nz : 3 * nz / 2;
     c->Lx = Lx; c->Lz = Lz; c->h = h[0]; c->g = g; c->M = M; c->m_run = M; c->prec = precision;
     c->opt.eps = 1.0; c->opt.integrator = ZK_RK4; c->opt.taper = 1; c->opt.filter = 1; c->opt.stream = nullptr;
     c->nb = nb;
@@ -1070,6 +1152,7 @@ void tile_view(const zk_ctx* g, int t, zk_ctx* v) {
     v->col = off(g->col, (size_t)t * g->tcol * g->csz);
     v->acc = off(g->acc, (size_t)t * g->tacc * ((g->prec == ZK_F32 && !g->series64) ? 4 : 8));
     v->series64 = g->series64;
+    v->pad3 = g->pad3;
     v->nfields = g->nfields;
     v->fstride = g->fstride;
     v->stage = g->stage; v->tank = g->tank;
@@ -1085,6 +1168,15 @@ extern "C" {
 
 zk_status zk_create(zk_ctx** out, int nx, int nz, double Lx, double Lz, double h, double g, int M, int precision) {
     return ctx_create(out, nx, nz, Lx, Lz, &h, 1, g, M, precision);
+}
+
+zk_status zk_create_ex(zk_ctx** out, int nx, int nz, double Lx, double Lz, double h, double g, int M, int precision,
+                       int pad) {
+    if (pad != ZK_PAD_3_2 && pad != ZK_PAD_3) {
+        if (out) *out = nullptr;
+        return ZK_EINVAL;
+    }
+    return ctx_create(out, nx, nz, Lx, Lz, &h, 1, g, M, precision, pad == ZK_PAD_3 ? 1 : 0);
 }
 
 zk_status zk_set_options(zk_ctx* c, const zk_options* o) {
@@ -1271,6 +1363,10 @@ zk_status zk_step(zk_ctx* c, double dt, int n) {
     if (c->closure_on && c->opt.integrator != ZK_RK4) return ZK_EUNSUPPORTED;
     cudaStream_t s = user_stream(c);
     for (int i = 0; i < n; ++i) {
+        if (c->adapt_every > 0 && c->nsteps % c->adapt_every == 0) {
+            zk_status st = c->prec == ZK_F32 ? Pipe<float>::adapt_check(c, s) : Pipe<double>::adapt_check(c, s);
+            if (st != ZK_OK) return st;
+        }
         if (c->closure_on && c->check_every > 0 && c->nsteps % c->check_every == 0) {
             zk_status st = Pipe<float>::closure_check(c, s);   // may switch the closure off
             if (st != ZK_OK) return st;
@@ -1394,8 +1490,8 @@ static zk_status closure_buffers(zk_ctx* c) {
     const size_t compact = (size_t)c->nz * c->hx * c->csz, plane = (size_t)c->nx * c->nz * sizeof(float);
     zk_status st = dalloc(c, &c->cspec, 6 * compact);
     if (st == ZK_OK) st = dalloc(c, &c->feat, 6 * plane);
-    if (st == ZK_OK) st = dalloc(c, &c->chk, 2 * compact);
-    if (st == ZK_OK) st = dalloc(c, (void**)&c->cpart, 2 * 256 * sizeof(double));
+    if (st == ZK_OK && !c->chk) st = dalloc(c, &c->chk, 2 * compact);
+    if (st == ZK_OK && !c->cpart) st = dalloc(c, (void**)&c->cpart, 2 * 256 * sizeof(double));
     return st;
 }
 
@@ -1441,7 +1537,7 @@ zk_status zk_closure_set(zk_ctx* c, zk_net* net, int base_order, const float* in
     if (base_order < 1 || base_order >= c->M || check_every < 0 || !(check_tol > 0) || !in_scale || !out_scale ||
         !scales_ok(in_scale, out_scale))
         return ZK_EINVAL;
-    if (c->prec != ZK_F32) return ZK_EUNSUPPORTED;
+    if (c->prec != ZK_F32 || c->adapt_every > 0) return ZK_EUNSUPPORTED;
     zk_status st = closure_buffers(c);
     if (st == ZK_OK) st = zk_net_reserve(net, (size_t)c->nx * c->nz);
     if (st != ZK_OK) return st;
@@ -1462,10 +1558,40 @@ zk_status zk_closure_set(zk_ctx* c, zk_net* net, int base_order, const float* in
 zk_status zk_set_series_fp64(zk_ctx* c, int on) {
     if (!c || (on != 0 && on != 1)) return ZK_EINVAL;
     if (c->prec != ZK_F32) return ZK_OK;   // FP64 contexts sum in FP64 already
+    if (c->pad3 && on) return ZK_EUNSUPPORTED;
     if (c->series64 != (on == 1)) {
         c->series64 = on == 1;
         drop_graph(c);
     }
+    return ZK_OK;
+}
+
+zk_status zk_set_adaptive_order(zk_ctx* c, int m_min, double tol, int check_every) {
+    if (!c || check_every < 0) return ZK_EINVAL;
+    if (check_every == 0) {
+        c->adapt_every = 0;
+        if (c->m_run != c->M) { c->m_run = c->M; drop_graph(c); }
+        return ZK_OK;
+    }
+    if (m_min < 1 || m_min > c->M || !(tol >= 0.0) || !std::isfinite(tol)) return ZK_EINVAL;
+    if (c->closure_on) return ZK_EUNSUPPORTED;
+    zk_status st = ZK_OK;
+    if (!c->chk) st = dalloc(c, &c->chk, 2 * (size_t)c->nz * c->hx * c->csz);
+    if (st == ZK_OK && !c->cpart) st = dalloc(c, (void**)&c->cpart, 2 * 256 * sizeof(double));
+    if (st != ZK_OK) return st;
+    c->adapt_every = check_every;
+    c->adapt_min = m_min;
+    c->adapt_tol = tol;
+    c->adapt_checks = 0;
+    c->nsteps = 0;
+    return ZK_OK;
+}
+
+zk_status zk_adaptive_status(const zk_ctx* c, int* order, int* checks, double* err) {
+    if (!c) return ZK_EINVAL;
+    if (order) *order = c->m_run > 0 ? c->m_run : c->M;
+    if (checks) *checks = c->adapt_checks;
+    if (err) for (int m = 1; m <= ZK_MAX_ORDER; ++m) err[m - 1] = c->adapt_err[m];
     return ZK_OK;
 }
 

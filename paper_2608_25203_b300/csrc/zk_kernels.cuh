@@ -79,6 +79,7 @@ struct RowArgs {
     int nb;                  // tiles in the launch (host side: grid.y)
     int occ;                 // host side: resident blocks per SM to use (0 = all)
     int acc64;               // host side: series sums in FP64 (FP32 contexts; acc holds doubles)
+    int pad3;                // host side: 3N padding (kernels with DIV = 6)
 };
 
 // ---------------------------------------------------------------------------
@@ -125,6 +126,7 @@ struct ColArgs {
     long long tcol, tst;
     const T* hb;                    // nullptr: every tile has depth h
     int nb;                         // tiles in the launch (host side: grid.y)
+    int pad3;                       // host side: 3N padding (kernels with DIV = 6)
 };
 
 static __global__ void energy_finalize_kernel(const double* __restrict__ partial, int n, double* __restrict__ out) {

@@ -35,11 +35,12 @@ template <> __device__ __forceinline__ void d_sincos<double>(double x, double* s
 #endif
 constexpr int kRowMaxThreads = ZK_ROW_MAX_THREADS;
 
-template <typename T, int NPX, int V = 0, typename TA = T>
+// DIV = NPX / (nx / 2): 3 for the 3/2 rule, 6 for the 3N padding.
+template <typename T, int NPX, int V = 0, typename TA = T, int DIV = 3>
 __global__ void __launch_bounds__(kRowMaxThreads) row2_kernel(const RowArgs<T> a, const cx<T>* __restrict__ tw) {
     using P = IPlan<NPX, V>;
     constexpr int TL = P::TL;
-    constexpr int HX = NPX / 3;
+    constexpr int HX = NPX / DIV;
     constexpr int LS = line_stride(NPX);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<T>* lines = reinterpret_cast<cx<T>*>(smem_raw);
@@ -186,12 +187,12 @@ __device__ __forceinline__ void col2_store_tile(const cx<T>* sm, int per, cx<T>*
     }
 }
 
-template <typename T, int NPZ, int CB, int V = 0>
+template <typename T, int NPZ, int CB, int V = 0, int DIV = 3>
 __global__ void __launch_bounds__(CB * IPlan<NPZ, V>::TL < 32 ? 32 : CB * IPlan<NPZ, V>::TL)
 col2_kernel(const ColArgs<T> a, const cx<T>* __restrict__ tw) {
     using P = IPlan<NPZ, V>;
     constexpr int TL = P::TL;
-    constexpr int NZ = 2 * NPZ / 3;
+    constexpr int NZ = 2 * NPZ / DIV;
     constexpr int LS = line_stride(NPZ);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
@@ -544,6 +545,37 @@ __global__ void closure_diff_kernel(const cx<T>* __restrict__ hi, const cx<T>* _
                                     long long n, ClosureScales sc) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < 2 * n; i += (long long)gridDim.x * blockDim.x)
         out[i] = cscale(csub(hi[i], lo[i]), (T)(1.0f / sc.out[i < n ? 0 : 1]));
+}
+
+// Adaptive order: FP64 sums over the half spectrum (kx > 0 columns weighted 2)
+// of |lo - hi|^2 and |hi|^2, both components, into part[2 * block].
+template <typename T>
+__global__ void diff_norm_kernel(const cx<T>* __restrict__ he, const cx<T>* __restrict__ hp,
+                                 const cx<T>* __restrict__ le, const cx<T>* __restrict__ lp, int nz, int hx,
+                                 double* __restrict__ part) {
+    const long long n = (long long)nz * hx;
+    double num = 0.0, den = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int col = (int)(i % hx);
+        const double w = col == 0 ? 1.0 : 2.0;
+        const cx<T> a = he[i], b = hp[i], c = le[i], d = lp[i];
+        const double ex = (double)c.x - a.x, ey = (double)c.y - a.y, px = (double)d.x - b.x, py = (double)d.y - b.y;
+        num += w * (ex * ex + ey * ey + px * px + py * py);
+        den += w * ((double)a.x * a.x + (double)a.y * a.y + (double)b.x * b.x + (double)b.y * b.y);
+    }
+    __shared__ double red[2][32];
+    for (int o = 16; o > 0; o >>= 1) {
+        num += __shfl_down_sync(0xffffffffu, num, o);
+        den += __shfl_down_sync(0xffffffffu, den, o);
+    }
+    if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = num; red[1][threadIdx.x >> 5] = den; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double x = 0.0, y = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { x += red[0][w]; y += red[1][w]; }
+        part[2 * blockIdx.x] = x;
+        part[2 * blockIdx.x + 1] = y;
+    }
 }
 
 // Fallback check: with D = f_high - f_low (d = 6 .. 1 / 2) and the predicted

@@ -20,13 +20,15 @@ LIB_PATH = os.path.join(HERE, "libzk.so")
 ZK_OK, ZK_EINVAL, ZK_ENOMEM, ZK_ECUDA, ZK_ENONFINITE, ZK_ETIMEOUT, ZK_EUNSUPPORTED, ZK_ESTATE = range(8)
 ZK_F32, ZK_F64 = 0, 1
 ZK_RK4, ZK_IFAB2 = 0, 1
+ZK_PAD_3_2, ZK_PAD_3 = 0, 1
 
 # every symbol include/zk.h declares
 EXPORTS = [
-    "zk_create", "zk_destroy", "zk_set_options", "zk_get_options", "zk_set_state", "zk_get_state",
+    "zk_create", "zk_create_ex", "zk_destroy", "zk_set_options", "zk_get_options", "zk_set_state", "zk_get_state",
     "zk_rhs", "zk_dno", "zk_step", "zk_energy", "zk_sync", "zk_device_bytes",
     "zk_launches_per_step", "zk_profile_step", "zk_dno_static", "zk_dno_inverse", "zk_relax",
-    "zk_set_state_tank", "zk_get_state_tank", "zk_set_series_fp64",
+    "zk_set_state_tank", "zk_get_state_tank", "zk_set_series_fp64", "zk_set_adaptive_order",
+    "zk_adaptive_status",
     "zk_batch_create", "zk_batch_destroy", "zk_batch_set_options", "zk_batch_set_state", "zk_batch_get_state",
     "zk_batch_energy", "zk_batch_step", "zk_batch_sync", "zk_batch_info", "zk_batch_group", "zk_batch_set_shape",
     "zk_batch_autotune",
@@ -66,6 +68,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     pd = ctypes.POINTER(ctypes.c_double)
     sig = {
         "zk_create": ([ctypes.POINTER(vp), i, i, d, d, d, d, i, i], i),
+        "zk_create_ex": ([ctypes.POINTER(vp), i, i, d, d, d, d, i, i, i], i),
         "zk_destroy": ([vp], None),
         "zk_set_options": ([vp, ctypes.POINTER(ZkOptions)], i),
         "zk_get_options": ([vp, ctypes.POINTER(ZkOptions)], i),
@@ -85,6 +88,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "zk_get_state_tank": ([vp, vp, vp, i, i], i),
         "zk_relax": ([vp, vp, vp, i, i, d, i], i),
         "zk_set_series_fp64": ([vp, i], i),
+        "zk_set_adaptive_order": ([vp, i, d, i], i),
+        "zk_adaptive_status": ([vp, ctypes.POINTER(i), ctypes.POINTER(i), pd], i),
         "zk_batch_create": ([ctypes.POINTER(vp), i, ctypes.POINTER(i), ctypes.POINTER(i), pd, pd, pd, d,
                              ctypes.POINTER(i), i], i),
         "zk_batch_destroy": ([vp], None),
@@ -148,6 +153,12 @@ def _ptr(x, dtype_code):
 def zk_create(nx, nz, Lx, Lz, h, g, M, precision=ZK_F32):
     c = ctypes.c_void_p()
     _check("zk_create", load().zk_create(ctypes.byref(c), nx, nz, Lx, Lz, h, g, M, precision))
+    return c
+
+
+def zk_create_ex(nx, nz, Lx, Lz, h, g, M, precision=ZK_F32, pad=ZK_PAD_3_2):
+    c = ctypes.c_void_p()
+    _check("zk_create_ex", load().zk_create_ex(ctypes.byref(c), nx, nz, Lx, Lz, h, g, M, precision, pad))
     return c
 
 
@@ -253,6 +264,17 @@ def zk_set_series_fp64(ctx, on=True):
     _check("zk_set_series_fp64", load().zk_set_series_fp64(ctx, 1 if on else 0))
 
 
+def zk_set_adaptive_order(ctx, m_min, tol, check_every):
+    _check("zk_set_adaptive_order", load().zk_set_adaptive_order(ctx, int(m_min), float(tol), int(check_every)))
+
+
+def zk_adaptive_status(ctx):
+    o, c = ctypes.c_int(), ctypes.c_int()
+    err = (ctypes.c_double * 8)()
+    _check("zk_adaptive_status", load().zk_adaptive_status(ctx, ctypes.byref(o), ctypes.byref(c), err))
+    return dict(order=o.value, checks=c.value, err=[err[m] for m in range(8)])
+
+
 def zk_dno_inverse(ctx, v, iters=8, dtype=None):
     dt = dtype if dtype is not None else _dtype_of(v)
     pv, dv = _ptr(v, dt)
@@ -299,9 +321,9 @@ class Zakharov:
     """One simulation context on the current CUDA device."""
 
     def __init__(self, nx, nz, Lx, Lz, h, g=9.81, M=5, precision=ZK_F32, eps=1.0, taper=True,
-                 filter=True, stream=None):
+                 filter=True, stream=None, pad=ZK_PAD_3_2):
         self.nx, self.nz, self.M, self.precision = nx, nz, M, precision
-        self.ctx = zk_create(nx, nz, Lx, Lz, h, g, M, precision)
+        self.ctx = zk_create_ex(nx, nz, Lx, Lz, h, g, M, precision, pad)
         self._stream = stream
         zk_set_options(self.ctx, eps=eps, taper=int(taper), filter=int(filter), stream=stream)
 
