@@ -49,6 +49,14 @@ the FP64 oracle at this size), FP32, and FP32 with FP64 series sums: eta and
 psi relative L2 against FP64, Hamiltonian difference, steps/s; and at 2048^2
 (the sea workload) the FP32 and FP32 + FP64-series throughput and their
 difference after 500 steps. value = FP32 eta error vs FP64 at 1024^2.
+
+--workload variants: accuracy / cost variants of the series on the sea
+workload's sea at 1024^2 (L = 800 m), RK4 dt = 0.02 s, FP32: exact
+de-aliasing (3N padding) against the 3/2 rule at M = 5 (ms/step, eta
+difference after 500 steps at eps = 0.5; steps survived at eps = 1, up to
+1000), and the adaptive order (maximum 6, minimum 2, check every 50 steps)
+against plain M = 6 (ms/step, orders chosen, eta error after 500 steps).
+value = steps survived at eps = 1 with 3N padding.
 """
 from __future__ import annotations
 
@@ -467,6 +475,90 @@ def precision_arm(args):
     return 0
 
 
+def variants_arm(args):
+    """Exact de-aliasing and adaptive order against the plain series."""
+    import numpy as np
+    import torch
+
+    from paper_2608_25203_b300 import seas
+    from paper_2608_25203_b300 import zk
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    stream = torch.cuda.current_stream()
+    n, L, h, dt = 1024, 800.0, W["h"], W["dt"]
+    eta, psi, _ = seas.jonswap_sea(n, n, L, L, h, W["Hs"], W["Tp"], W["seed"])
+    e32, p32 = eta.astype(np.float32), psi.astype(np.float32)
+
+    def make(M, eps, pad=0):
+        s = zk.Zakharov(n, n, L, L, h, W["g"], M, zk.ZK_F32, eps=eps, stream=stream.cuda_stream, pad=pad)
+        s.set_state(e32, p32)
+        return s
+
+    def timed(s, steps):
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        s.step(dt, steps)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        return t0.elapsed_time(t1) / steps
+
+    def survive(M, pad, limit=1000, chunk=5):
+        s = make(M, 1.0, pad)
+        done = 0
+        while done < limit:
+            s.step(dt, chunk)
+            done += chunk
+            try:
+                s.energy()
+            except zk.ZkError:
+                s.close()
+                return done - chunk
+        s.close()
+        return limit
+
+    out = {}
+    steps = args.frames or 500
+    # exact de-aliasing vs 3/2 at M = 5
+    runs = {}
+    for name, pad in (("pad_3_2", zk.ZK_PAD_3_2), ("pad_3", zk.ZK_PAD_3)):
+        s = make(5, W["eps"], pad)
+        s.step(dt, 3)
+        s.set_state(e32, p32)
+        ms = timed(s, steps)
+        runs[name] = (ms, s.get_state()[0])
+        s.close()
+    e_a, e_b = runs["pad_3_2"][1], runs["pad_3"][1]
+    out["dealias"] = {"ms_pad_3_2": runs["pad_3_2"][0], "ms_pad_3": runs["pad_3"][0],
+                      "eta_rel_diff_after_%d" % steps: float(np.linalg.norm(e_a - e_b) / np.linalg.norm(e_b)),
+                      "eps1_steps_survived_pad_3_2": survive(5, zk.ZK_PAD_3_2),
+                      "eps1_steps_survived_pad_3": survive(5, zk.ZK_PAD_3)}
+    # adaptive order vs plain M = 6
+    ref = make(6, W["eps"])
+    ref.step(dt, 3)
+    ref.set_state(e32, p32)
+    ms6 = timed(ref, steps)
+    e6 = ref.get_state()[0]
+    ref.close()
+    ad = {"ms_plain_M6": ms6}
+    for tol in (1e-3, 1e-4, 1e-5):
+        s = make(6, W["eps"])
+        zk.zk_set_adaptive_order(s.ctx, 2, tol, 50)
+        ms = timed(s, steps)
+        st = zk.zk_adaptive_status(s.ctx)
+        e = s.get_state()[0]
+        ad["tol_%g" % tol] = {"ms": ms, "order": st["order"], "checks": st["checks"],
+                              "rhs_rel_diff_by_order": st["err"][:6],
+                              "eta_rel_err_vs_M6": float(np.linalg.norm(e - e6) / np.linalg.norm(e6))}
+        s.close()
+    out["adaptive"] = ad
+    print(json.dumps({"metric": "series variants: RK4 steps survived at eps=1 with exact de-aliasing (1024^2, M=5)",
+                      "value": out["dealias"]["eps1_steps_survived_pad_3"], "unit": "steps", "higher_is_better": True,
+                      "steps": steps, "dtype": "f32", "data": "synthetic", "n_gpus": 1,
+                      "config": {"workload": WORKLOAD.replace("2048x2048, L=1600 m", "1024x1024, L=800 m")},
+                      "results": out}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -476,7 +568,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--profile-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="sea", choices=["sea", "tank", "batch", "closure", "precision"])
+    ap.add_argument("--workload", default="sea", choices=["sea", "tank", "batch", "closure", "precision",
+                                                                "variants"])
     ap.add_argument("--frames", type=int, default=None,
                     help="timed steps of --workload tank (default 2000 per case) or batch (default 200)")
     args = ap.parse_args()
@@ -488,6 +581,8 @@ def main():
         return closure_arm(args)
     if args.workload == "precision":
         return precision_arm(args)
+    if args.workload == "variants":
+        return variants_arm(args)
     if args.impl == "reference":
         return reference_arm(args)
     if args.warmup < 3:
