@@ -57,6 +57,11 @@ difference after 500 steps at eps = 0.5; steps survived at eps = 1, up to
 1000), and the adaptive order (maximum 6, minimum 2, check every 50 steps)
 against plain M = 6 (ms/step, orders chosen, eta error after 500 steps).
 value = steps survived at eps = 1 with 3N padding.
+
+--workload netinfer: the closure network's inference alone at 2048^2 (one
+sample, 6 -> 32 -> 32 -> 32 -> 2), on the tensor cores and on the SIMT kernels;
+value = tensor-core TFLOP/s (FLOPs of the padded K the MMAs execute), with the
+roofline against the measured dense bf16 peak (FP16 runs at the same rate).
 """
 from __future__ import annotations
 
@@ -559,6 +564,50 @@ def variants_arm(args):
     return 0
 
 
+def netinfer_arm(args):
+    """Closure-network inference on the tensor cores vs the SIMT kernels."""
+    import numpy as np
+    import torch
+
+    from paper_2608_25203_b300 import zk
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    stream = torch.cuda.current_stream()
+    n, reps = 2048, args.frames or 20
+    rng = np.random.default_rng(0)
+    net = zk.Net((0.05 * rng.standard_normal(20322)).astype(np.float32))
+    x = torch.from_numpy(rng.standard_normal((6, n, n)).astype(np.float32)).cuda()
+    y = torch.empty((2, n, n), device="cuda")
+    flop = n * n * 2 * (9 * 16 * 32 + 2 * 9 * 32 * 32 + 32 * 2)   # padded K of the three 3x3 layers + 1x1
+    out = {}
+    for name, mode in (("tensor_cores", 1), ("simt", 0)):
+        net.set_inference(mode)
+        for _ in range(3):
+            net.predict(x, y, stream.cuda_stream)
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(reps):
+            zk.zk_net_predict(net.n, x, y, stream.cuda_stream)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1) / reps
+        out[name] = {"ms": ms, "TFLOPs": flop / ms / 1e9}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peak, src = float(json.load(f)["bf16_tflops"]), "measured"
+    except Exception:
+        peak, src = 1800.0, "fallback"
+    a = out["tensor_cores"]["TFLOPs"]
+    print(json.dumps({"metric": "closure-network inference, 2048^2, tensor cores", "value": a, "unit": "TFLOP/s",
+                      "higher_is_better": True, "steps": reps, "dtype": "f16 in / f32 acc", "data": "synthetic",
+                      "n_gpus": 1, "config": {"workload": "conv net 6-32-32-32-2 (3x3, 3x3, 3x3, 1x1), one 2048^2 sample"},
+                      "roofline": {"bound": "tensor", "achieved": a, "peak": peak, "unit": "TFLOP/s", "frac": a / peak,
+                                   "peak_source": src, "kernel": "conv3_tc_kernel"},
+                      "results": out}), flush=True)
+    net.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -569,7 +618,7 @@ def main():
     ap.add_argument("--profile-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="sea", choices=["sea", "tank", "batch", "closure", "precision",
-                                                                "variants"])
+                                                                "variants", "netinfer"])
     ap.add_argument("--frames", type=int, default=None,
                     help="timed steps of --workload tank (default 2000 per case) or batch (default 200)")
     args = ap.parse_args()
@@ -583,6 +632,8 @@ def main():
         return precision_arm(args)
     if args.workload == "variants":
         return variants_arm(args)
+    if args.workload == "netinfer":
+        return netinfer_arm(args)
     if args.impl == "reference":
         return reference_arm(args)
     if args.warmup < 3:
