@@ -100,6 +100,22 @@ zk_status zk_set_state(zk_ctx *ctx, const void *eta, const void *psi, int dtype,
 /* Copy the current state out as physical eta, psi [nz][nx]. Synchronises. */
 zk_status zk_get_state(zk_ctx *ctx, void *eta, void *psi, int dtype, int on_device);
 
+/* Asynchronous state I/O with pinned host buffers (same layouts as
+ * zk_set_state / zk_get_state, host pointers only). The copies run on two copy
+ * streams of the context (uploads, downloads) through two staging slots per
+ * direction, so the
+ * upload of the next state and the download of the last one overlap the
+ * context's kernels on its stream; neither call waits. zk_set_state_async:
+ * the host arrays must stay unchanged until the upload is done (zk_sync).
+ * zk_get_state_async: the host arrays hold the state as of the call once
+ * zk_sync has returned. zk_io_join makes the context's stream wait for every
+ * copy issued so far (no host wait), e.g. before recording a timing event.
+ * Host memory that is not page-locked makes the copies synchronous. Errors as
+ * for zk_set_state / zk_get_state; the first call allocates the staging slots. */
+zk_status zk_set_state_async(zk_ctx *ctx, const void *eta, const void *psi, int dtype);
+zk_status zk_get_state_async(zk_ctx *ctx, void *eta, void *psi, int dtype);
+zk_status zk_io_join(zk_ctx *ctx);
+
 /* Right-hand side of Eqs. 4 and 10 at the current state, as physical fields
  * [nz][nx]: d eta/dt = G(eta) psi (mean set to zero), d psi/dt. Synchronises. */
 zk_status zk_rhs(zk_ctx *ctx, void *deta_dt, void *dpsi_dt, int dtype, int on_device);

@@ -108,6 +108,13 @@ struct zk_ctx {
     int m_run = 0;                         // order of the right-hand side being enqueued (<= M)
     bool series64 = false;                 // FP32 context: series sums and accumulator in FP64
     bool pad3 = false;                     // padded grid 3N (exact series products) instead of 3N/2
+    // asynchronous host I/O: copies on their own stream through two staging slots per direction
+    cudaStream_t io = nullptr, io_out = nullptr;   // uploads, downloads (separate, so that they overlap)
+    cudaEvent_t ev_in[2] = {}, ev_in_used[2] = {}, ev_out[2] = {}, ev_out_done[2] = {};
+    bool in_used_rec[2] = {false, false}, out_done_rec[2] = {false, false};
+    void* astage_in[2] = {nullptr, nullptr};
+    void* astage_out[2] = {nullptr, nullptr};
+    int in_slot = 0, out_slot = 0;
     // learned closure (FP32): order-base_M right-hand side plus the network's residual
     zk_net* net = nullptr;
     bool closure_on = false;
@@ -1066,6 +1073,16 @@ void zk_destroy(zk_ctx* c) {
     if (!c) return;
     drop_graph(c);
     if (c->cap) cudaStreamDestroy(c->cap);
+    if (c->io) {
+        cudaStreamSynchronize(c->io);
+        cudaStreamSynchronize(c->io_out);
+        cudaStreamDestroy(c->io);
+        cudaStreamDestroy(c->io_out);
+        for (int k = 0; k < 2; ++k) {
+            cudaEventDestroy(c->ev_in[k]); cudaEventDestroy(c->ev_in_used[k]);
+            cudaEventDestroy(c->ev_out[k]); cudaEventDestroy(c->ev_out_done[k]);
+        }
+    }
     for (void* p : c->allocs) cudaFree(p);
     delete c;
 }
@@ -1470,7 +1487,103 @@ zk_status zk_profile_step(zk_ctx* c, double dt, int nsteps, double* ms, int* kin
 
 zk_status zk_sync(zk_ctx* c) {
     if (!c) return ZK_EINVAL;
+    if (c->io && (cudaStreamSynchronize(c->io) != cudaSuccess || cudaStreamSynchronize(c->io_out) != cudaSuccess))
+        return ZK_ECUDA;
     return cu(cudaStreamSynchronize(user_stream(c)));
+}
+
+static zk_status async_io_setup(zk_ctx* c) {
+    if (c->io) return ZK_OK;
+    const size_t slot = (size_t)2 * c->nx * c->nz * kIoElem;
+    zk_status st = ZK_OK;
+    for (int k = 0; k < 2 && st == ZK_OK; ++k) {
+        st = dalloc(c, &c->astage_in[k], slot);
+        if (st == ZK_OK) st = dalloc(c, &c->astage_out[k], slot);
+    }
+    if (st != ZK_OK) return st;
+    for (int k = 0; k < 2; ++k) {
+        cudaEvent_t* ev[4] = {&c->ev_in[k], &c->ev_in_used[k], &c->ev_out[k], &c->ev_out_done[k]};
+        for (cudaEvent_t* e : ev)
+            if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) return ZK_ECUDA;
+    }
+    if (cudaStreamCreateWithFlags(&c->io_out, cudaStreamNonBlocking) != cudaSuccess) { c->io_out = nullptr; return ZK_ECUDA; }
+    if (cudaStreamCreateWithFlags(&c->io, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaStreamDestroy(c->io_out);
+        c->io = c->io_out = nullptr;
+        return ZK_ECUDA;
+    }
+    return ZK_OK;
+}
+
+zk_status zk_set_state_async(zk_ctx* c, const void* eta, const void* psi, int dtype) {
+    if (!c || !eta || !psi || (dtype != ZK_F32 && dtype != ZK_F64)) return ZK_EINVAL;
+    zk_status st = async_io_setup(c);
+    if (st != ZK_OK) return st;
+    const int k = c->in_slot;
+    c->in_slot ^= 1;
+    cudaStream_t s = user_stream(c);
+    const size_t n = (size_t)c->nx * c->nz * (dtype == ZK_F32 ? 4 : 8);
+    char* a = (char*)c->astage_in[k];
+    char* b = a + (size_t)c->nx * c->nz * kIoElem;
+    cudaError_t e = cudaSuccess;
+    if (c->in_used_rec[k]) e = cudaStreamWaitEvent(c->io, c->ev_in_used[k], 0);   // the slot's last reader is done
+    if (e == cudaSuccess) e = cudaMemcpyAsync(a, eta, n, cudaMemcpyHostToDevice, c->io);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b, psi, n, cudaMemcpyHostToDevice, c->io);
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_in[k], c->io);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, c->ev_in[k], 0);
+    if (e == cudaSuccess)
+        e = c->prec == ZK_F32 ? Pipe<float>::set_state(c, a, b, dtype, s) : Pipe<double>::set_state(c, a, b, dtype, s);
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_in_used[k], s);
+    if (e != cudaSuccess) return ZK_ECUDA;
+    c->in_used_rec[k] = true;
+    c->has_state = true;
+    c->ab_valid = false;
+    return ZK_OK;
+}
+
+zk_status zk_get_state_async(zk_ctx* c, void* eta, void* psi, int dtype) {
+    if (!c || !eta || !psi || (dtype != ZK_F32 && dtype != ZK_F64)) return ZK_EINVAL;
+    if (!c->has_state) return ZK_ESTATE;
+    zk_status st = async_io_setup(c);
+    if (st != ZK_OK) return st;
+    const int k = c->out_slot;
+    c->out_slot ^= 1;
+    cudaStream_t s = user_stream(c);
+    const size_t n = (size_t)c->nx * c->nz * (dtype == ZK_F32 ? 4 : 8);
+    const size_t compact = (size_t)c->nz * c->hx * c->csz;
+    char* a = (char*)c->astage_out[k];
+    char* b = a + (size_t)c->nx * c->nz * kIoElem;
+    cudaError_t e = cudaSuccess;
+    if (c->out_done_rec[k]) e = cudaStreamWaitEvent(s, c->ev_out_done[k], 0);     // the slot's last download is done
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->ko_eta, c->y_eta, compact, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->ko_psi, c->y_psi, compact, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess)
+        e = c->prec == ZK_F32
+            ? Pipe<float>::to_physical(c, (cx<float>*)c->ko_eta, (cx<float>*)c->ko_psi, a, b, dtype, s)
+            : Pipe<double>::to_physical(c, (cx<double>*)c->ko_eta, (cx<double>*)c->ko_psi, a, b, dtype, s);
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_out[k], s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->io_out, c->ev_out[k], 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(eta, a, n, cudaMemcpyDeviceToHost, c->io_out);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(psi, b, n, cudaMemcpyDeviceToHost, c->io_out);
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_out_done[k], c->io_out);
+    if (e != cudaSuccess) return ZK_ECUDA;
+    c->out_done_rec[k] = true;
+    return ZK_OK;
+}
+
+zk_status zk_io_join(zk_ctx* c) {
+    if (!c) return ZK_EINVAL;
+    if (!c->io) return ZK_OK;
+    cudaError_t r = cudaSuccess;
+    for (cudaStream_t q : {c->io, c->io_out}) {
+        cudaEvent_t e;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return ZK_ECUDA;
+        r = cudaEventRecord(e, q);
+        if (r == cudaSuccess) r = cudaStreamWaitEvent(user_stream(c), e, 0);
+        cudaEventDestroy(e);
+        if (r != cudaSuccess) break;
+    }
+    return cu(r);
 }
 
 zk_status zk_device_bytes(const zk_ctx* c, size_t* b) {

@@ -24,7 +24,7 @@ ZK_PAD_3_2, ZK_PAD_3 = 0, 1
 
 # every symbol include/zk.h declares
 EXPORTS = [
-    "zk_create", "zk_create_ex", "zk_destroy", "zk_set_options", "zk_get_options", "zk_set_state", "zk_get_state",
+    "zk_create", "zk_create_ex", "zk_set_state_async", "zk_get_state_async", "zk_io_join", "zk_destroy", "zk_set_options", "zk_get_options", "zk_set_state", "zk_get_state",
     "zk_rhs", "zk_dno", "zk_step", "zk_energy", "zk_sync", "zk_device_bytes",
     "zk_launches_per_step", "zk_profile_step", "zk_dno_static", "zk_dno_inverse", "zk_relax",
     "zk_set_state_tank", "zk_get_state_tank", "zk_set_series_fp64", "zk_set_adaptive_order",
@@ -69,6 +69,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     sig = {
         "zk_create": ([ctypes.POINTER(vp), i, i, d, d, d, d, i, i], i),
         "zk_create_ex": ([ctypes.POINTER(vp), i, i, d, d, d, d, i, i, i], i),
+        "zk_set_state_async": ([vp, vp, vp, i], i),
+        "zk_get_state_async": ([vp, vp, vp, i], i),
+        "zk_io_join": ([vp], i),
         "zk_destroy": ([vp], None),
         "zk_set_options": ([vp, ctypes.POINTER(ZkOptions)], i),
         "zk_get_options": ([vp, ctypes.POINTER(ZkOptions)], i),
@@ -242,6 +245,30 @@ def zk_profile_step(ctx, dt, nsteps=1, cap=256):
                                                      ctypes.byref(n)))
     k = n.value
     return list(ms[:k]), [KERNEL_CLASSES[x] for x in kind[:k]], list(by[:k])
+
+
+def zk_set_state_async(ctx, eta, psi, dtype=None):
+    """Upload from pinned host arrays (torch pinned tensors or numpy arrays) without waiting."""
+    dt = dtype if dtype is not None else _dtype_of(eta)
+    pe, de = _ptr(eta, dt)
+    pp, dp = _ptr(psi, dt)
+    if de or dp:
+        raise ValueError("host arrays expected")
+    _check("zk_set_state_async", load().zk_set_state_async(ctx, pe, pp, dt))
+
+
+def zk_get_state_async(ctx, eta, psi, dtype=None):
+    """Download into pinned host arrays without waiting (valid after zk_sync)."""
+    dt = dtype if dtype is not None else _dtype_of(eta)
+    pe, de = _ptr(eta, dt)
+    pp, dp = _ptr(psi, dt)
+    if de or dp:
+        raise ValueError("host arrays expected")
+    _check("zk_get_state_async", load().zk_get_state_async(ctx, pe, pp, dt))
+
+
+def zk_io_join(ctx):
+    _check("zk_io_join", load().zk_io_join(ctx))
 
 
 def zk_set_state_tank(ctx, eta, psi, dtype=None):
