@@ -15,8 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libzk.so")
 SOURCES = [os.path.join(HERE, "csrc", f) for f in ("zk_api.cu", "zk_static.cu", "zk_net.cu")]
-DEPS = SOURCES + [os.path.join(HERE, "csrc", f) for f in ("zk_fft.cuh", "zk_kernels.cuh", "zk_fft2.cuh", "zk_kernels2.cuh", "zk_net_internal.h")] + \
-    [os.path.join(ROOT, "include", "zk.h")]
+DEPS = sorted(os.path.join(HERE, "csrc", f) for f in os.listdir(os.path.join(HERE, "csrc"))
+              if f.endswith((".cu", ".cuh", ".h"))) + [os.path.join(ROOT, "include", "zk.h")]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
