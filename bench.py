@@ -84,6 +84,32 @@ WORKLOAD = ("JONSWAP sea 2048x2048, L=1600 m, h=50 m, M=5, eps=0.5, RK4 dt=0.02 
 FALLBACK_HBM = 6400.0
 
 
+def rank_env():
+    """(rank, world size, local rank) from the launcher's environment (1 rank without one)."""
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def replica_seed(rank):
+    """Each rank advances its own sea (independent replicas, weak scaling): seed 3 + rank."""
+    return W["seed"] + rank
+
+
+def max_over_ranks(value, dist=None, device="cuda"):
+    """The largest value over all ranks (a job's time is its slowest rank's time)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(steps, world, ms):
+    """Whole-job steps/s: every rank takes `steps` steps of its own sea within the slowest rank's ms."""
+    return steps * world / (ms / 1e3)
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -642,9 +668,7 @@ def main():
     import numpy as np
     import torch
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank, world, local = rank_env()
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -655,7 +679,7 @@ def main():
     from paper_2608_25203_b300 import zk
 
     eta, psi, info = seas.jonswap_sea(W["nx"], W["nz"], W["Lx"], W["Lz"], W["h"], W["Hs"], W["Tp"],
-                                      W["seed"] + rank)
+                                      replica_seed(rank))
     eta32 = np.ascontiguousarray(eta, dtype=np.float32)
     psi32 = np.ascontiguousarray(psi, dtype=np.float32)
     stream = torch.cuda.current_stream()
@@ -685,15 +709,13 @@ def main():
     clk = clocks.stop()
     if dist:
         dist.barrier()
-        m = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(m, op=dist.ReduceOp.MAX)
-        ms = float(m.item())
+    ms = max_over_ranks(ms, dist)
     try:
         H, _, _, _ = sim.energy()
         finite = math.isfinite(H)
     except zk.ZkError:
         finite = False
-    value = args.steps * world / (ms / 1e3)
+    value = job_rate(args.steps, world, ms)
     ms_per_step = ms / args.steps
 
     # ---- per-launch roofline (CUDA events between launches) -----------------
@@ -740,13 +762,9 @@ def main():
     zk.zk_io_join(sim.ctx)
     e1.record(stream)
     torch.cuda.synchronize()
-    ems = e0.elapsed_time(e1)
-    if dist:
-        m = torch.tensor([ems], device="cuda", dtype=torch.float64)
-        dist.all_reduce(m, op=dist.ReduceOp.MAX)
-        ems = float(m.item())
+    ems = max_over_ranks(e0.elapsed_time(e1), dist)
     nbytes = 2 * W["nx"] * W["nz"] * 4
-    e2e = {"value": args.e2e_steps * world / (ems / 1e3), "unit": "steps/s", "h2d_bytes_per_step": nbytes,
+    e2e = {"value": job_rate(args.e2e_steps, world, ems), "unit": "steps/s", "h2d_bytes_per_step": nbytes,
            "d2h_bytes_per_step": nbytes}
 
     cpu = None
