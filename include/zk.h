@@ -234,7 +234,7 @@ zk_status zk_set_series_fp64(zk_ctx *ctx, int on);
  * f_M at the current state and then f_m for m = m_min, m_min + 1, ... and
  * steps at the first m with |f_m - f_M| <= tol |f_M| (L2 over both spectra,
  * FP64 sums), or at M if none qualifies. zk_rhs, zk_dno and zk_energy use the
- * chosen order too. Checks synchronise the stream and cost up to
+ * chosen order too; a change of order restarts the IF-AB2 history (IF-Euler). Checks synchronise the stream and cost up to
  * M - m_min + 1 right-hand sides. check_every = 0 switches it off (order M
  * again). ZK_EINVAL for m_min outside [1, M] or tol < 0; ZK_EUNSUPPORTED while
  * a closure is attached. */

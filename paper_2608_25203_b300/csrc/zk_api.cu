@@ -786,6 +786,7 @@ struct Pipe {
         ++c->adapt_checks;
         if (chosen != before) {
             c->m_run = chosen;
+            c->ab_valid = false;   // IF-AB2 history holds forcing of the old order: restart with IF-Euler
             drop_graph(c);
         }
         return ZK_OK;

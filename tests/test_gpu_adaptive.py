@@ -88,3 +88,20 @@ def test_adaptive_arguments(zk, sea):
     with pytest.raises(zk.ZkError) as e:
         zk.zk_closure_set(s.ctx, net.n, 2, np.ones(6), np.ones(2))
     assert e.value.status == zk.ZK_EUNSUPPORTED
+
+
+def test_ifab2_with_adaptive_order_matches_oracle(zk, sea):
+    # a tolerance that every order meets: the first check switches 6 -> 2 before the
+    # first step, so the run is the order-2 IF-AB2 run from its IF-Euler bootstrap
+    s = zk.Zakharov(N, N, L, L, H, M=6, eps=1.0, precision=zk.ZK_F64)
+    zk.zk_set_options(s.ctx, eps=1.0, integrator=zk.ZK_IFAB2)
+    s.set_state(sea[0].astype(np.float64), sea[1].astype(np.float64))
+    zk.zk_set_adaptive_order(s.ctx, 2, 1e30, 100)
+    s.step(0.02, 10)
+    o = Oracle(Grid(N, N, L, L, H), 2, eps=1.0)
+    eh, ph = o.spectrum(sea[0].astype(np.float64)), o.spectrum(sea[1].astype(np.float64))
+    hist = None
+    for _ in range(10):
+        eh, ph, hist = o.step_ifab2(eh, ph, 0.02, hist)
+    ge, gp = s.get_state()
+    assert np.linalg.norm(ge - o.physical(eh)) / np.linalg.norm(o.physical(eh)) < 1e-10
