@@ -31,9 +31,10 @@ states the steps:
 * taper exp[-(|k|/kc)^8], kc = (2/3) kNyq, on every forward-transformed
   nonlinear quantity (Sec. 6.1; reading: kNyq = pi / max(dx, dz)).
 * (d eta/dt)_{k=0} := 0 (reading: every G_j has zero mean).
-* classical RK4 (the workload's integrator) or the paper's integrating-factor
-  AB2 with IF-Euler bootstrap (Sec. 3.4, Eqs. 13-16), each followed by the
-  state filter A(k) (Eq. 17) once per step.
+* classical RK4 (the workload's integrator), the paper's integrating-factor
+  AB2 with IF-Euler bootstrap (Sec. 3.4, Eqs. 13-16), or integrating-factor
+  RK4 (Lawson's form, the linear rotation of Eq. 14 exact), each followed by
+  the state filter A(k) (Eq. 17) once per step.
 * the Hamiltonian (Eq. 1) by Parseval.
 
 Every function here is pinned by a CPU test (closed forms, invariants, brute
@@ -289,6 +290,33 @@ class Oracle:
         c, sw, G0sw, gsw, _, _ = self.if_coeffs(dt)
         return c * eh + G0sw * ph, -gsw * eh + c * ph
 
+    def step_ifrk4(self, eh: np.ndarray, ph: np.ndarray, dt: float):
+        """Integrating-factor RK4 (Lawson's form): the linear part of Eq. 13 exactly, via the
+        rotation E_t of Eq. 14, the nonlinear part N by classical RK4 in the rotating frame:
+            k1 = N(y), k2 = N(E_{h/2}(y + h/2 k1)), k3 = N(E_{h/2} y + h/2 k2),
+            k4 = N(E_h y + h E_{h/2} k3),
+            y' = E_h y + h/6 (E_h k1 + 2 E_{h/2} (k2 + k3) + k4),
+        then the state filter (Eq. 17) once per step."""
+        h = dt
+        E = self.linear_propagate
+
+        def N(e, p):
+            _, (Fe, Fp) = self.rhs_parts(e, p)
+            return Fe, Fp
+
+        k1 = N(eh, ph)
+        k2 = N(*E(eh + 0.5 * h * k1[0], ph + 0.5 * h * k1[1], 0.5 * h))
+        yh = E(eh, ph, 0.5 * h)
+        k3 = N(yh[0] + 0.5 * h * k2[0], yh[1] + 0.5 * h * k2[1])
+        yf = E(eh, ph, h)
+        k3h = E(k3[0], k3[1], 0.5 * h)
+        k4 = N(yf[0] + h * k3h[0], yf[1] + h * k3h[1])
+        k1f = E(k1[0], k1[1], h)
+        k23 = E(k2[0] + k3[0], k2[1] + k3[1], 0.5 * h)
+        e1 = yf[0] + h / 6.0 * (k1f[0] + 2.0 * k23[0] + k4[0])
+        p1 = yf[1] + h / 6.0 * (k1f[1] + 2.0 * k23[1] + k4[1])
+        return self.apply_filter(e1, p1)
+
     # ---- state recovery and the relaxation source (Secs. 3.5 and 5) -----------
     def dno_inverse(self, eh: np.ndarray, vh: np.ndarray, iters: int = 8, ph0: np.ndarray = None):
         """Inverse DNO map of Eq. 19 by fixed-point iteration.
@@ -379,6 +407,8 @@ def run(oracle: Oracle, eta: np.ndarray, psi: np.ndarray, dt: float, nsteps: int
             eh, ph = oracle.step_rk4(eh, ph, dt)
         elif integrator == "ifab2":
             eh, ph, hist = oracle.step_ifab2(eh, ph, dt, hist)
+        elif integrator == "ifrk4":
+            eh, ph = oracle.step_ifrk4(eh, ph, dt)
         else:
             raise ValueError(integrator)
         if callback is not None:
