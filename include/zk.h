@@ -50,11 +50,11 @@ typedef enum {
 } zk_status;
 
 enum { ZK_F32 = 0, ZK_F64 = 1 };               /* element types of I/O arrays and of the compute path */
-enum { ZK_RK4 = 0, ZK_IFAB2 = 1 };             /* time integrators */
+enum { ZK_RK4 = 0, ZK_IFAB2 = 1, ZK_IFRK4 = 2 };   /* time integrators */
 
 typedef struct {
     double eps;        /* nonlinear-amplitude parameter of Eqs. 9-11, in [0, 1]; default 1 */
-    int integrator;    /* ZK_RK4 (default) or ZK_IFAB2 (Sec. 3.4, Eqs. 15-16) */
+    int integrator;    /* ZK_RK4 (default), ZK_IFAB2 (Sec. 3.4, Eqs. 15-16) or ZK_IFRK4 */
     int taper;         /* 1 (default): taper exp[-(|k|/kc)^8] on nonlinear products (Sec. 6.1) */
     int filter;        /* 1 (default): state filter A(k) of Eq. 17 once per step */
     void *stream;      /* cudaStream_t for all launches; NULL = legacy default stream */
@@ -160,6 +160,10 @@ zk_status zk_relax(zk_ctx *ctx, const void *sigma, const void *eta_target, int d
  * the nonlinear forcing enters through Eqs. 15-16 with F* = 3/2 F_n - 1/2 F_{n-1};
  * the first step after zk_set_state, after an option change, or with a dt
  * different from the previous step's uses F* = F_n (IF-Euler bootstrap).
+ * ZK_IFRK4 evaluates it four times: integrating-factor RK4 in Lawson's form,
+ * the linear rotation of Eq. 14 applied exactly over h/2 and h, classical RK4
+ * stages on the nonlinear part in the rotating frame (fourth order, exact
+ * linear dispersion; needs no history).
  * ZK_ESTATE before zk_set_state. */
 zk_status zk_step(zk_ctx *ctx, double dt, int n);
 

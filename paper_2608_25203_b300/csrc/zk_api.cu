@@ -611,6 +611,9 @@ struct Pipe {
                 case FIN_RK1: b += 4 * Cc; break;                 // ka, ys written (state is y)
                 case FIN_RK2: case FIN_RK3: b += 8 * Cc; break;   // y, ka read; ka, ys written
                 case FIN_RK4: b += 6 * Cc; break;                 // y, ka read; y written
+                case FIN_IRK1: b += 6 * Cc; break;                // y read; ka, ys written
+                case FIN_IRK2: case FIN_IRK3: b += 8 * Cc; break; // y, ka read; ka, ys written
+                case FIN_IRK4: b += 6 * Cc; break;                // y, ka read; y written
                 default: break;
                 }
                 note(c, s, ZK_K_COL_FINAL, b);
@@ -836,6 +839,23 @@ struct Pipe {
         return e;
     }
 
+    // Integrating-factor RK4: four right-hand sides, Lawson stage combination in the epilogue.
+    static cudaError_t ifrk4_step(zk_ctx* c, double dt, cudaStream_t s, int* nlaunch) {
+        for (int st = 1; st <= 4; ++st) {
+            ColArgs<T> fin = col_base(c);
+            fin.mode = FIN_IRK1 + st - 1;
+            fin.dt = (T)dt;
+            fin.y_eta = C(c->y_eta); fin.y_psi = C(c->y_psi);
+            fin.ys_eta = C(c->ys_eta); fin.ys_psi = C(c->ys_psi);
+            fin.ka_eta = C(c->ka_eta); fin.ka_psi = C(c->ka_psi);
+            const cx<T>* se = st == 1 ? C(c->y_eta) : C(c->ys_eta);
+            const cx<T>* sp = st == 1 ? C(c->y_psi) : C(c->ys_psi);
+            cudaError_t e = rhs(c, se, sp, fin, s, nlaunch);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
+
     static cudaError_t ifab2_step(zk_ctx* c, double dt, bool first, cudaStream_t s, int* nlaunch) {
         ColArgs<T> fin = col_base(c);
         fin.mode = FIN_IFAB2;
@@ -988,6 +1008,8 @@ void drop_graph(zk_ctx* c) {
 // variant: 0 = RK4 step, 1 = IF-AB2 bootstrap step, 2 = IF-AB2 step with history
 cudaError_t enqueue_step_any(zk_ctx* c, double dt, cudaStream_t s, int* nl, int variant) {
     if (variant == 0) {
+        if (c->opt.integrator == ZK_IFRK4)
+            return c->prec == ZK_F32 ? Pipe<float>::ifrk4_step(c, dt, s, nl) : Pipe<double>::ifrk4_step(c, dt, s, nl);
         if (c->closure_on && c->prec == ZK_F32) return Pipe<float>::closure_rk4_step(c, dt, s, nl);
         return c->prec == ZK_F32 ? Pipe<float>::rk4_step(c, dt, s, nl) : Pipe<double>::rk4_step(c, dt, s, nl);
     }
@@ -1200,7 +1222,7 @@ zk_status zk_create_ex(zk_ctx** out, int nx, int nz, double Lx, double Lz, doubl
 zk_status zk_set_options(zk_ctx* c, const zk_options* o) {
     if (!c || !o) return ZK_EINVAL;
     if (!(o->eps >= 0.0 && o->eps <= 1.0)) return ZK_EINVAL;
-    if (o->integrator != ZK_RK4 && o->integrator != ZK_IFAB2) return ZK_EINVAL;
+    if (o->integrator != ZK_RK4 && o->integrator != ZK_IFAB2 && o->integrator != ZK_IFRK4) return ZK_EINVAL;
     if ((o->taper != 0 && o->taper != 1) || (o->filter != 0 && o->filter != 1)) return ZK_EINVAL;
     if (o->integrator != c->opt.integrator || o->eps != c->opt.eps || o->taper != c->opt.taper)
         c->ab_valid = false;   // the forcing history belongs to the old right-hand side

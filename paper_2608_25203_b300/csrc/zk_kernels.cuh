@@ -88,7 +88,7 @@ struct RowArgs {
 enum ColKind { COL_FROM_STATE = 0, COL_PHI = 1, COL_FINAL = 2 };
 enum ColSym { SYM_ID = 0, SYM_DZ = 1, SYM_ZA = 2 };
 enum FinalMode { FIN_RHS = 0, FIN_RK1 = 1, FIN_RK2 = 2, FIN_RK3 = 3, FIN_RK4 = 4, FIN_ENERGY = 5, FIN_IFAB2 = 6,
-                 FIN_INVDNO = 7 };
+                 FIN_INVDNO = 7, FIN_IRK1 = 8, FIN_IRK2 = 9, FIN_IRK3 = 10, FIN_IRK4 = 11 };
 
 template <typename T>
 struct ColArgs {

@@ -377,6 +377,58 @@ col2_kernel(const ColArgs<T> a, const cx<T>* __restrict__ tw) {
         case FIN_RHS:
             a.ko_eta[idx] = de; a.ko_psi[idx] = dp;
             break;
+        case FIN_IRK1:
+        case FIN_IRK2:
+        case FIN_IRK3:
+        case FIN_IRK4: {
+            // Integrating-factor RK4 (Lawson): the linear flow E_t of Eq. 14 exactly, RK4 on
+            // the nonlinear part k = (Fe, Fp) of this stage in the rotating frame.
+            const T w = d_sqrt(a.g * G0);
+            T c1, s1, c2, s2;                          // cos and sin/w of w h/2 and of w h
+            if (w > (T)0) {
+                T sh, ch;
+                d_sincos((T)0.5 * w * a.dt, &sh, &ch);
+                c1 = ch; s1 = sh / w;
+                c2 = (T)1 - (T)2 * sh * sh; s2 = (T)2 * sh * ch / w;
+            } else {                                   // k = 0: E_t (e, p) = (e, p - g t e)
+                c1 = 1; s1 = (T)0.5 * a.dt; c2 = 1; s2 = a.dt;
+            }
+            auto rot_e = [&](cx<T> e, cx<T> pp, T c, T sw) { return cadd(cscale(e, c), cscale(pp, G0 * sw)); };
+            auto rot_p = [&](cx<T> e, cx<T> pp, T c, T sw) { return csub(cscale(pp, c), cscale(e, a.g * sw)); };
+            const T hh = a.dt;
+            const cx<T> ye = a.y_eta[idx], yp = a.y_psi[idx];
+            if (a.mode == FIN_IRK1) {
+                a.ka_eta[idx] = rot_e(Fe, Fp, c2, s2);
+                a.ka_psi[idx] = rot_p(Fe, Fp, c2, s2);
+                const cx<T> ue = cadd(ye, cscale(Fe, (T)0.5 * hh)), up = cadd(yp, cscale(Fp, (T)0.5 * hh));
+                a.ys_eta[idx] = rot_e(ue, up, c1, s1);
+                a.ys_psi[idx] = rot_p(ue, up, c1, s1);
+            } else if (a.mode == FIN_IRK2) {
+                a.ka_eta[idx] = cadd(a.ka_eta[idx], cscale(rot_e(Fe, Fp, c1, s1), (T)2));
+                a.ka_psi[idx] = cadd(a.ka_psi[idx], cscale(rot_p(Fe, Fp, c1, s1), (T)2));
+                a.ys_eta[idx] = cadd(rot_e(ye, yp, c1, s1), cscale(Fe, (T)0.5 * hh));
+                a.ys_psi[idx] = cadd(rot_p(ye, yp, c1, s1), cscale(Fp, (T)0.5 * hh));
+            } else if (a.mode == FIN_IRK3) {
+                const cx<T> ke = rot_e(Fe, Fp, c1, s1), kp = rot_p(Fe, Fp, c1, s1);
+                a.ka_eta[idx] = cadd(a.ka_eta[idx], cscale(ke, (T)2));
+                a.ka_psi[idx] = cadd(a.ka_psi[idx], cscale(kp, (T)2));
+                a.ys_eta[idx] = cadd(rot_e(ye, yp, c2, s2), cscale(ke, hh));
+                a.ys_psi[idx] = cadd(rot_p(ye, yp, c2, s2), cscale(kp, hh));
+            } else {
+                T A = 1;
+                if (a.filter) {
+                    const T rx = (T)col / (T)a.hx;
+                    const T rz = (T)(mz < 0 ? -mz : mz) / (T)(NZ / 2);
+                    A = (T)0.125 * ((T)5 + (T)4 * d_cospi(rx) - d_cospi((T)2 * rx)) *
+                        ((T)0.125 * ((T)5 + (T)4 * d_cospi(rz) - d_cospi((T)2 * rz)));
+                }
+                const T w6 = hh / (T)6;
+                const cx<T> ne = cadd(rot_e(ye, yp, c2, s2), cscale(cadd(a.ka_eta[idx], Fe), w6));
+                const cx<T> np = cadd(rot_p(ye, yp, c2, s2), cscale(cadd(a.ka_psi[idx], Fp), w6));
+                a.y_eta[idx] = cscale(ne, A);
+                a.y_psi[idx] = cscale(np, A);
+            }
+        } break;
         case FIN_RK1: {
             a.ka_eta[idx] = de; a.ka_psi[idx] = dp;
             const T hd = (T)0.5 * a.dt;

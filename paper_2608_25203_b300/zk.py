@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "libzk.so")
 
 ZK_OK, ZK_EINVAL, ZK_ENOMEM, ZK_ECUDA, ZK_ENONFINITE, ZK_ETIMEOUT, ZK_EUNSUPPORTED, ZK_ESTATE = range(8)
 ZK_F32, ZK_F64 = 0, 1
-ZK_RK4, ZK_IFAB2 = 0, 1
+ZK_RK4, ZK_IFAB2, ZK_IFRK4 = 0, 1, 2
 ZK_PAD_3_2, ZK_PAD_3 = 0, 1
 
 # every symbol include/zk.h declares
