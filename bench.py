@@ -48,14 +48,18 @@ for 500 RK4 steps in FP64 (the reference; one right-hand side checked against
 the FP64 oracle at this size), FP32, and FP32 with FP64 series sums: eta and
 psi relative L2 against FP64, Hamiltonian difference, steps/s; and at 2048^2
 (the sea workload) the FP32 and FP32 + FP64-series throughput and their
-difference after 500 steps. value = FP32 eta error vs FP64 at 1024^2.
+difference after 500 steps. Both sizes also run the split-precision DFT-GEMM
+forms (innermost radix-8 stage of the padded transforms on the tensor cores,
+BF16 x3 and FP16 x3). value = FP32 eta error vs FP64 at 1024^2.
 
 --workload variants: accuracy / cost variants of the series on the sea
 workload's sea at 1024^2 (L = 800 m), RK4 dt = 0.02 s, FP32: exact
 de-aliasing (3N padding) against the 3/2 rule at M = 5 (ms/step, eta
 difference after 500 steps at eps = 0.5; steps survived at eps = 1, up to
 1000), and the adaptive order (maximum 6, minimum 2, check every 50 steps)
-against plain M = 6 (ms/step, orders chosen, eta error after 500 steps).
+against plain M = 6 (ms/step, orders chosen, eta error after 500 steps), and
+the integrators (RK4, IF-AB2, IF-RK4) over T = 8 s at dt = 0.02 .. 0.8 s:
+FP64 eta error against IF-RK4 at dt = 0.005 s (filter off), FP32 ms/step.
 value = steps survived at eps = 1 with 3N padding.
 
 --workload netinfer: the closure network's inference alone at 2048^2 (one
@@ -449,11 +453,13 @@ def precision_arm(args):
     steps = args.frames or 500
     dt, eps, M, h = W["dt"], W["eps"], W["M"], W["h"]
 
-    def run(n, L, prec, s64, nsteps):
+    def run(n, L, prec, s64, nsteps, dft=0):
         eta, psi, _ = seas.jonswap_sea(n, n, L, L, h, W["Hs"], W["Tp"], W["seed"])
         s = zk.Zakharov(n, n, L, L, h, W["g"], M, prec, eps=eps, stream=stream.cuda_stream)
         if s64:
             zk.zk_set_series_fp64(s.ctx, True)
+        if dft:
+            zk.zk_set_dft_precision(s.ctx, dft)
         e32, p32 = eta.astype(np.float32), psi.astype(np.float32)
         s.set_state(e32, p32) if prec == zk.ZK_F32 else s.set_state(e32.astype(np.float64), p32.astype(np.float64))
         s.step(dt, 3)
@@ -486,8 +492,9 @@ def precision_arm(args):
            "psi_rhs_rel": float(np.linalg.norm(gp - o.physical(dp)) / np.linalg.norm(o.physical(dp))),
            "oracle_s": t_orc}
     out["1024"] = {"fp64": {"ms": ms64, "H": ref_H}, "fp64_vs_oracle_one_rhs": orc}
-    for name, s64 in (("fp32", False), ("fp32_series64", True)):
-        e, p, H, ms, _ = run(n, L, zk.ZK_F32, s64, steps)
+    for name, s64, dft in (("fp32", False, 0), ("fp32_series64", True, 0),
+                           ("fp32_dft_bf16x3", False, zk.ZK_DFT_BF16X3), ("fp32_dft_fp16x3", False, zk.ZK_DFT_FP16X3)):
+        e, p, H, ms, _ = run(n, L, zk.ZK_F32, s64, steps, dft)
         out["1024"][name] = {"ms": ms, "eta_rel": float(np.linalg.norm(e - ref_e) / np.linalg.norm(ref_e)),
                              "psi_rel": float(np.linalg.norm(p - ref_p) / np.linalg.norm(ref_p)),
                              "H_rel": abs(H - ref_H) / ref_H}
@@ -498,12 +505,83 @@ def precision_arm(args):
                    "eta_rel_diff": float(np.linalg.norm(a[0] - b[0]) / np.linalg.norm(b[0])),
                    "psi_rel_diff": float(np.linalg.norm(a[1] - b[1]) / np.linalg.norm(b[1])),
                    "fp64": "not supported at 2048^2 (FP64 contexts up to 1024^2)"}
+    for name, dft in (("dft_bf16x3", zk.ZK_DFT_BF16X3), ("dft_fp16x3", zk.ZK_DFT_FP16X3)):
+        c = run(n, L, zk.ZK_F32, False, steps, dft)
+        out["2048"][name] = {"ms": c[3],
+                             "eta_rel_diff_vs_fp32_series64": float(np.linalg.norm(c[0] - b[0]) / np.linalg.norm(b[0])),
+                             "psi_rel_diff_vs_fp32_series64": float(np.linalg.norm(c[1] - b[1]) / np.linalg.norm(b[1]))}
     print(json.dumps({"metric": "precision study: eta rel L2 vs FP64 after %d RK4 steps (1024^2, M=5)" % steps,
                       "value": out["1024"]["fp32"]["eta_rel"], "unit": "rel L2", "higher_is_better": False,
                       "steps": steps, "dtype": "f32/f64", "data": "synthetic", "n_gpus": 1,
                       "config": {"workload": WORKLOAD.replace("2048x2048, L=1600 m", "1024x1024 (L=800 m) and 2048x2048")},
                       "results": out}), flush=True)
     return 0
+
+
+def integrator_study(n, L, h, eta, psi, e32, p32, stream):
+    """RK4, IF-AB2 and IF-RK4 over the same simulated time T = 8 s at M = 5, eps = 0.5.
+
+    The cost of a step does not depend on dt, so the FP32 ms per simulated second is the
+    measured ms per step over dt; with the errors it gives accuracy at equal cost.
+
+    Accuracy in FP64 (so that FP32 rounding does not hide a fourth-order error): eta relative
+    L2 error at T against IF-RK4 at dt = 0.005 s. The state filter is off for this study, since
+    it acts once per step and would make runs of different dt differ by the number of filter
+    applications; the taper stays on. Cost in FP32: ms per step, 100 steps at dt = 0.02 s."""
+    import numpy as np
+    import torch
+
+    from paper_2608_25203_b300 import zk
+
+    T, M, eps = 8.0, 5, W["eps"]
+    kinds = (("rk4", zk.ZK_RK4), ("ifab2", zk.ZK_IFAB2), ("ifrk4", zk.ZK_IFRK4))
+
+    def make(precision, integrator):
+        s = zk.Zakharov(n, n, L, L, h, W["g"], M, precision, eps=eps, filter=False, stream=stream.cuda_stream)
+        zk.zk_set_options(s.ctx, eps=eps, integrator=integrator, taper=1, filter=0, stream=stream.cuda_stream)
+        return s
+
+    def run_to_T(integrator, dtx):
+        s = make(zk.ZK_F64, integrator)
+        s.set_state(eta, psi)
+        steps = int(round(T / dtx))
+        s.step(dtx, steps)
+        try:
+            s.energy()
+            e = s.get_state()[0]
+        except zk.ZkError:
+            e = None
+        s.close()
+        return e if e is not None and np.all(np.isfinite(e)) else None
+
+    ref = run_to_T(zk.ZK_IFRK4, 0.005)
+    alt = run_to_T(zk.ZK_RK4, 0.005)
+    res = {"T_s": T, "reference": "IF-RK4, dt = 0.005 s, FP64", "filter": "off",
+           "reference_vs_rk4_same_dt": (None if ref is None or alt is None
+                                        else float(np.linalg.norm(alt - ref) / np.linalg.norm(ref))),
+           "eta_rel_err": {}, "ms_per_simulated_s_f32": {}}
+    dts = (0.02, 0.05, 0.1, 0.2, 0.4, 0.8)
+    for name, kind in kinds:
+        errs = {}
+        for dtx in dts:
+            e = run_to_T(kind, dtx)
+            errs["dt_%g" % dtx] = (None if e is None or ref is None
+                                   else float(np.linalg.norm(e - ref) / np.linalg.norm(ref)))
+        res["eta_rel_err"][name] = errs
+        s = make(zk.ZK_F32, kind)
+        s.set_state(e32, p32)
+        s.step(0.02, 5)
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        s.step(0.02, 100)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1) / 100
+        res.setdefault("ms_per_step_f32", {})[name] = ms
+        res["ms_per_simulated_s_f32"][name] = {"dt_%g" % dtx: ms / dtx for dtx in dts}
+        s.close()
+    return res
 
 
 def variants_arm(args):
@@ -582,6 +660,7 @@ def variants_arm(args):
                               "eta_rel_err_vs_M6": float(np.linalg.norm(e - e6) / np.linalg.norm(e6))}
         s.close()
     out["adaptive"] = ad
+    out["integrators"] = integrator_study(n, L, h, eta, psi, e32, p32, stream)
     print(json.dumps({"metric": "series variants: RK4 steps survived at eps=1 with exact de-aliasing (1024^2, M=5)",
                       "value": out["dealias"]["eps1_steps_survived_pad_3"], "unit": "steps", "higher_is_better": True,
                       "steps": steps, "dtype": "f32", "data": "synthetic", "n_gpus": 1,

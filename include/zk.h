@@ -50,7 +50,7 @@ typedef enum {
 } zk_status;
 
 enum { ZK_F32 = 0, ZK_F64 = 1 };               /* element types of I/O arrays and of the compute path */
-enum { ZK_RK4 = 0, ZK_IFAB2 = 1, ZK_IFRK4 = 2 };   /* time integrators */
+enum { ZK_RK4 = 0, ZK_IFRK4 = 1, ZK_IFAB2 = 2 };   /* time integrators */
 
 typedef struct {
     double eps;        /* nonlinear-amplitude parameter of Eqs. 9-11, in [0, 1]; default 1 */
@@ -231,6 +231,24 @@ zk_status zk_dno_static(const float *eta, const float *psi, float *v, int nx, in
  * transforms and the stored fields stay FP32. on = 0 restores the FP32 sums.
  * FP64 contexts ignore the call (ZK_OK). ZK_EINVAL for other values of on. */
 zk_status zk_set_series_fp64(zk_ctx *ctx, int on);
+
+/* Split-precision DFT-GEMM stages (the precision form of the padded
+ * transforms; the paper computes in FP32 on the GPU, Sec. 4.3, and names mixed-precision
+ * FFT pipelines as future work, Sec. 9). mode ZK_DFT_F32 (default): every
+ * stage of the padded line transforms is an FP32 butterfly. ZK_DFT_BF16X3 /
+ * ZK_DFT_FP16X3: the innermost radix-8 stage of every padded row and column
+ * transform of the right-hand side is a matrix product with the length-8 DFT
+ * matrix (as the real 16 x 16 matrix [[Fr, -Fi], [Fi, Fr]]) on the tensor
+ * cores, each FP32 operand split into a 16-bit high and low part (BF16, or
+ * FP16 with a power-of-two scale per 8-point block) and three products
+ * summed in FP32. The other stages, the
+ * unpadded state transforms and all pointwise arithmetic stay FP32. Needs an
+ * FP32 context with the 3/2 rule, FP32 series sums and padded lengths 1536 or
+ * 3072 on both axes (nx, nz in {1024, 2048}), else ZK_EUNSUPPORTED;
+ * ZK_EINVAL for other modes. While a split mode is set, zk_set_series_fp64(1)
+ * returns ZK_EUNSUPPORTED. */
+enum { ZK_DFT_F32 = 0, ZK_DFT_BF16X3 = 1, ZK_DFT_FP16X3 = 2 };
+zk_status zk_set_dft_precision(zk_ctx *ctx, int mode);
 
 /* Adaptive order (the adaptive-order scheme Sec. 9 lists as future work, in
  * its global form): the context keeps its order M as the maximum. Every

@@ -105,6 +105,7 @@ struct zk_ctx {
     // launch shape (set by the batch autotuner): plan variant, columns-per-block
     // choice (0 / 1 / 2 = half / default / double), row blocks per SM (0 = all resident)
     int plan_v = 0, col_ci = 1, row_occ = 0;
+    int dft_split = 0;                     // ZK_DFT_*: innermost radix-8 stage on the tensor cores
     int m_run = 0;                         // order of the right-hand side being enqueued (<= M)
     bool series64 = false;                 // FP32 context: series sums and accumulator in FP64
     bool pad3 = false;                     // padded grid 3N (exact series products) instead of 3N/2
@@ -169,6 +170,11 @@ struct zk_ctx {
 namespace {
 
 cudaStream_t user_stream(const zk_ctx* c) { return (cudaStream_t)c->opt.stream; }
+// Plan variant of the padded transforms: the split-precision DFT-GEMM plans
+// (SPLIT_BF16 / SPLIT_FP16) when selected, else the tuned FP32 plan.
+int plan_of(const zk_ctx* c) {
+    return c->dft_split == ZK_DFT_BF16X3 ? SPLIT_BF16 : c->dft_split == ZK_DFT_FP16X3 ? SPLIT_FP16 : c->plan_v;
+}
 void drop_graph(zk_ctx* c);
 
 zk_status cu(cudaError_t e) { return e == cudaSuccess ? ZK_OK : ZK_ECUDA; }
@@ -233,6 +239,19 @@ cudaError_t launch_row_t(const RowArgs<T>& a, const cx<T>* tw, int npz, cudaStre
 
 template <typename T>
 cudaError_t launch_row(int npx, int v, const RowArgs<T>& a, const cx<T>* tw, int npz, cudaStream_t s) {
+    if (v == SPLIT_BF16 || v == SPLIT_FP16) {   // FP32 3/2-rule plans of the long lines only
+        if constexpr (sizeof(T) == 4) {
+            if (a.pad3 || a.acc64) return cudaErrorInvalidValue;
+            switch (npx * 4 + v) {
+            case 1536 * 4 + SPLIT_BF16: return launch_row_t<T, 1536, SPLIT_BF16>(a, tw, npz, s);
+            case 3072 * 4 + SPLIT_BF16: return launch_row_t<T, 3072, SPLIT_BF16>(a, tw, npz, s);
+            case 1536 * 4 + SPLIT_FP16: return launch_row_t<T, 1536, SPLIT_FP16>(a, tw, npz, s);
+            case 3072 * 4 + SPLIT_FP16: return launch_row_t<T, 3072, SPLIT_FP16>(a, tw, npz, s);
+            default: break;
+            }
+        }
+        return cudaErrorInvalidValue;
+    }
     if constexpr (sizeof(T) == 4) {
         if (a.pad3) {    // 3N padding: FP32, default plans and sums
             switch (npx) {
@@ -314,6 +333,24 @@ cudaError_t launch_col_v(int ci, const ColArgs<T>& a, const cx<T>* tw, cudaStrea
 template <typename T>
 cudaError_t launch_col(int npz, int v, int ci, const ColArgs<T>& a, const cx<T>* tw, cudaStream_t s,
                        int* nblocks = nullptr) {
+    if (v == SPLIT_BF16 || v == SPLIT_FP16) {   // default blocking; FP32 3/2-rule plans of the long lines
+        if constexpr (sizeof(T) == 4) {
+            constexpr int ES = (int)sizeof(cx<T>);
+            if (a.pad3) return cudaErrorInvalidValue;
+            switch (npz * 4 + v) {
+            case 1536 * 4 + SPLIT_BF16:
+                return launch_col_t<T, 1536, col_cb<1536, ES, SPLIT_BF16>(), SPLIT_BF16>(a, tw, s, nblocks);
+            case 3072 * 4 + SPLIT_BF16:
+                return launch_col_t<T, 3072, col_cb<3072, ES, SPLIT_BF16>(), SPLIT_BF16>(a, tw, s, nblocks);
+            case 1536 * 4 + SPLIT_FP16:
+                return launch_col_t<T, 1536, col_cb<1536, ES, SPLIT_FP16>(), SPLIT_FP16>(a, tw, s, nblocks);
+            case 3072 * 4 + SPLIT_FP16:
+                return launch_col_t<T, 3072, col_cb<3072, ES, SPLIT_FP16>(), SPLIT_FP16>(a, tw, s, nblocks);
+            default: break;
+            }
+        }
+        return cudaErrorInvalidValue;
+    }
     if constexpr (sizeof(T) == 4) {
         if (a.pad3) {    // 3N padding: FP32, default plans and blocking
             constexpr int ES = (int)sizeof(cx<T>);
@@ -538,7 +575,7 @@ struct Pipe {
             for (int q = 1; q <= M; ++q) out(F.z(0, q), 1, SYM_ZA, q);
             a.nout = o;
             note(c, s, ZK_K_COL_STATE, 2 * Cc + o * U);
-            if ((e = launch_col<T>(c->npz, c->plan_v, c->col_ci, a, twz, s)) != cudaSuccess) return e;
+            if ((e = launch_col<T>(c->npz, plan_of(c), c->col_ci, a, twz, s)) != cudaSuccess) return e;
             ++nl;
         }
         for (int r = 1; r <= M - 1; ++r) {
@@ -561,7 +598,7 @@ struct Pipe {
                 const double wr = U + (r >= 2 ? Pp : 0.0);
                 note(c, s, ZK_K_ROW_ROUND, rd + wr);
             }
-            if ((e = launch_row<T>(c->npx, c->plan_v, ra, twx, c->npz, s)) != cudaSuccess) return e;
+            if ((e = launch_row<T>(c->npx, plan_of(c), ra, twx, c->npz, s)) != cudaSuccess) return e;
             ++nl;
             ColArgs<T> a = col_base(c);
             a.kind = COL_PHI;
@@ -572,7 +609,7 @@ struct Pipe {
             }
             a.nout = o;
             note(c, s, ZK_K_COL_PHI, (1 + o) * U);
-            if ((e = launch_col<T>(c->npz, c->plan_v, c->col_ci, a, twz, s)) != cudaSuccess) return e;
+            if ((e = launch_col<T>(c->npz, plan_of(c), c->col_ci, a, twz, s)) != cudaSuccess) return e;
             ++nl;
         }
         {
@@ -594,7 +631,7 @@ struct Pipe {
             ra.out0 = C(c->col) + (long long)F.gnl() * c->fstride;
             ra.out1 = C(c->col) + (long long)F.npsi() * c->fstride;
             note(c, s, ZK_K_ROW_FINAL, (5 + (M >= 2 ? M : 0) + 2) * U + (M >= 3 ? Pp : 0.0));
-            if ((e = launch_row<T>(c->npx, c->plan_v, ra, twx, c->npz, s)) != cudaSuccess) return e;
+            if ((e = launch_row<T>(c->npx, plan_of(c), ra, twx, c->npz, s)) != cudaSuccess) return e;
             ++nl;
         }
         {
@@ -618,7 +655,7 @@ struct Pipe {
                 }
                 note(c, s, ZK_K_COL_FINAL, b);
             }
-            if ((e = launch_col<T>(c->npz, c->plan_v, c->col_ci, fin, twz, s, &c->fin_blocks)) != cudaSuccess) return e;
+            if ((e = launch_col<T>(c->npz, plan_of(c), c->col_ci, fin, twz, s, &c->fin_blocks)) != cudaSuccess) return e;
             ++nl;
         }
         if (nlaunch) *nlaunch += nl;
@@ -1694,9 +1731,27 @@ zk_status zk_closure_set(zk_ctx* c, zk_net* net, int base_order, const float* in
 zk_status zk_set_series_fp64(zk_ctx* c, int on) {
     if (!c || (on != 0 && on != 1)) return ZK_EINVAL;
     if (c->prec != ZK_F32) return ZK_OK;   // FP64 contexts sum in FP64 already
-    if (c->pad3 && on) return ZK_EUNSUPPORTED;
+    if ((c->pad3 || c->dft_split != ZK_DFT_F32) && on) return ZK_EUNSUPPORTED;
     if (c->series64 != (on == 1)) {
         c->series64 = on == 1;
+        drop_graph(c);
+    }
+    return ZK_OK;
+}
+
+zk_status zk_set_dft_precision(zk_ctx* c, int mode) {
+    if (!c || mode < ZK_DFT_F32 || mode > ZK_DFT_FP16X3) return ZK_EINVAL;
+    if (mode != ZK_DFT_F32) {
+        auto long_line = [](int n) { return n == 1536 || n == 3072; };
+        if (c->prec != ZK_F32 || c->pad3 || c->series64 || c->nb > 1 || !long_line(c->npx) || !long_line(c->npz))
+            return ZK_EUNSUPPORTED;
+    }
+    if (c->dft_split != mode) {
+        c->dft_split = mode;
+        // the split plans keep the radices, and so the twiddle tables, of the default plan
+        const int v = mode != ZK_DFT_F32 ? 0 : c->plan_v;
+        c->tw_px = c->tw_pv[v][0];
+        c->tw_pz = c->tw_pv[v][1];
         drop_graph(c);
     }
     return ZK_OK;

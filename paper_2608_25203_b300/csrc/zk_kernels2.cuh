@@ -7,7 +7,7 @@
 // column after a DIT) are in natural order.
 #pragma once
 
-#include "zk_fft2.cuh"
+#include "zk_dftmma.cuh"
 #include "zk_kernels.cuh"
 
 namespace zk {

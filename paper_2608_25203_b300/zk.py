@@ -19,15 +19,17 @@ LIB_PATH = os.path.join(HERE, "libzk.so")
 
 ZK_OK, ZK_EINVAL, ZK_ENOMEM, ZK_ECUDA, ZK_ENONFINITE, ZK_ETIMEOUT, ZK_EUNSUPPORTED, ZK_ESTATE = range(8)
 ZK_F32, ZK_F64 = 0, 1
-ZK_RK4, ZK_IFAB2, ZK_IFRK4 = 0, 1, 2
+ZK_RK4, ZK_IFRK4, ZK_IFAB2 = 0, 1, 2
 ZK_PAD_3_2, ZK_PAD_3 = 0, 1
+ZK_DFT_F32, ZK_DFT_BF16X3, ZK_DFT_FP16X3 = 0, 1, 2
 
 # every symbol include/zk.h declares
 EXPORTS = [
     "zk_create", "zk_create_ex", "zk_set_state_async", "zk_get_state_async", "zk_io_join", "zk_destroy", "zk_set_options", "zk_get_options", "zk_set_state", "zk_get_state",
     "zk_rhs", "zk_dno", "zk_step", "zk_energy", "zk_sync", "zk_device_bytes",
     "zk_launches_per_step", "zk_profile_step", "zk_dno_static", "zk_dno_inverse", "zk_relax",
-    "zk_set_state_tank", "zk_get_state_tank", "zk_set_series_fp64", "zk_set_adaptive_order",
+    "zk_set_state_tank", "zk_get_state_tank", "zk_set_series_fp64", "zk_set_dft_precision",
+    "zk_set_adaptive_order",
     "zk_adaptive_status",
     "zk_batch_create", "zk_batch_destroy", "zk_batch_set_options", "zk_batch_set_state", "zk_batch_get_state",
     "zk_batch_energy", "zk_batch_step", "zk_batch_sync", "zk_batch_info", "zk_batch_group", "zk_batch_set_shape",
@@ -39,7 +41,10 @@ EXPORTS = [
     "zk_strerror", "zk_version",
 ]
 
-KERNEL_CLASSES = {0: "col_state", 1: "row_round", 2: "col_phi", 3: "row_final", 4: "col_final"}
+ZK_K_COL_STATE, ZK_K_ROW_ROUND, ZK_K_COL_PHI, ZK_K_ROW_FINAL, ZK_K_COL_FINAL = range(5)
+ZK_MAX_ORDER = 8
+KERNEL_CLASSES = {ZK_K_COL_STATE: "col_state", ZK_K_ROW_ROUND: "row_round", ZK_K_COL_PHI: "col_phi",
+                  ZK_K_ROW_FINAL: "row_final", ZK_K_COL_FINAL: "col_final"}
 
 
 class ZkOptions(ctypes.Structure):
@@ -91,6 +96,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "zk_get_state_tank": ([vp, vp, vp, i, i], i),
         "zk_relax": ([vp, vp, vp, i, i, d, i], i),
         "zk_set_series_fp64": ([vp, i], i),
+        "zk_set_dft_precision": ([vp, i], i),
         "zk_set_adaptive_order": ([vp, i, d, i], i),
         "zk_adaptive_status": ([vp, ctypes.POINTER(i), ctypes.POINTER(i), pd], i),
         "zk_batch_create": ([ctypes.POINTER(vp), i, ctypes.POINTER(i), ctypes.POINTER(i), pd, pd, pd, d,
@@ -289,6 +295,10 @@ def zk_get_state_tank(ctx, eta, psi, dtype=None):
 
 def zk_set_series_fp64(ctx, on=True):
     _check("zk_set_series_fp64", load().zk_set_series_fp64(ctx, 1 if on else 0))
+
+
+def zk_set_dft_precision(ctx, mode):
+    _check("zk_set_dft_precision", load().zk_set_dft_precision(ctx, int(mode)))
 
 
 def zk_set_adaptive_order(ctx, m_min, tol, check_every):

@@ -37,6 +37,33 @@ def test_binding_lists_every_symbol():
     assert declared_symbols() == set(zk.EXPORTS)
 
 
+def test_binding_constants_match_header():
+    """Every ZK_* constant the header defines (enum members and #defines) has the same value in
+    the Python binding."""
+    from paper_2608_25203_b300 import zk
+    txt = "".join(open(os.path.join(ROOT, "include", f)).read()
+                  for f in os.listdir(os.path.join(ROOT, "include")) if f.endswith(".h"))
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    consts = {}
+    for body in re.findall(r"enum\s*\{([^}]*)\}", txt):
+        nxt = 0
+        for item in body.split(","):
+            item = item.strip()
+            if not item:
+                continue
+            name, _, val = item.partition("=")
+            nxt = int(val, 0) if val.strip() else nxt
+            consts[name.strip()] = nxt
+            nxt += 1
+    for name, val in re.findall(r"#define\s+(ZK_[A-Z0-9_]+)\s+(-?\d+)\b", txt):
+        consts[name] = int(val)
+    consts = {k: v for k, v in consts.items() if k.startswith("ZK_")}
+    assert {"ZK_RK4", "ZK_IFRK4", "ZK_IFAB2", "ZK_F32", "ZK_PAD_3"} <= set(consts)
+    assert (consts["ZK_RK4"], consts["ZK_IFRK4"], consts["ZK_IFAB2"]) == (0, 1, 2)
+    wrong = {k: (v, getattr(zk, k, None)) for k, v in consts.items() if getattr(zk, k, None) != v}
+    assert not wrong, wrong
+
+
 def test_host_only_entry_points(lib):
     lib.zk_version.restype = ctypes.c_char_p
     lib.zk_strerror.restype = ctypes.c_char_p
