@@ -187,8 +187,17 @@ __device__ __forceinline__ void col2_store_tile(const cx<T>* sm, int per, cx<T>*
     }
 }
 
+// Where the final pass's two lines per column leave room for a single block per SM (over half
+// of the SM's shared memory), say so to the compiler: it may then use the registers that
+// occupancy leaves free instead of spilling. 0 leaves the minimum unspecified.
+template <typename T, int NPZ, int CB>
+constexpr int col_min_blocks() {
+    return (size_t)CB * col_stride(2 * line_stride(NPZ)) * sizeof(cx<T>) > 116 * 1024 ? 1 : 0;
+}
+
 template <typename T, int NPZ, int CB, int V = 0, int DIV = 3>
-__global__ void __launch_bounds__(CB * IPlan<NPZ, V>::TL < 32 ? 32 : CB * IPlan<NPZ, V>::TL)
+__global__ void __launch_bounds__(CB * IPlan<NPZ, V>::TL < 32 ? 32 : CB * IPlan<NPZ, V>::TL,
+                                  col_min_blocks<T, NPZ, CB>())
 col2_kernel(const ColArgs<T> a, const cx<T>* __restrict__ tw) {
     using P = IPlan<NPZ, V>;
     constexpr int TL = P::TL;
