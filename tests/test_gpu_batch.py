@@ -36,8 +36,9 @@ def _fields(t):
     return e.astype(np.float32), p.astype(np.float32)
 
 
-@pytest.mark.parametrize("integrator", [0, 1])
-def test_batch_bitwise_equals_single_contexts(zk, integrator):
+@pytest.mark.parametrize("name", ["rk4", "ifab2", "ifrk4"])
+def test_batch_bitwise_equals_single_contexts(zk, name):
+    integrator = {"rk4": zk.ZK_RK4, "ifab2": zk.ZK_IFAB2, "ifrk4": zk.ZK_IFRK4}[name]
     T = _tiles()
     b = zk.Batch(T, eps=0.5, integrator=integrator)
     assert b.info()[0] == 3
