@@ -375,7 +375,7 @@ zk_status zk_net_predict(zk_net *n, const float *x, float *y, int nz, int nx, vo
 zk_status zk_closure_features(zk_ctx *ctx, int base_order, const float *in_scale, const float *out_scale, float *feat,
                               float *target);
 /* Attach net (NULL detaches) to an FP32 context with the scales it was trained
- * with. From then on zk_step (RK4 only; ZK_EUNSUPPORTED for IF-AB2), zk_rhs and
+ * with. From then on zk_step (RK4 only; ZK_EUNSUPPORTED for IF-AB2 and IF-RK4), zk_rhs and
  * zk_dno use f_closure. Every check_every steps (0 = never), before the step,
  * the context computes f_M and f_b at the current state and the relative L2
  * error of the predicted residual against f_M - f_b; above check_tol the
