@@ -105,3 +105,21 @@ def test_ifab2_with_adaptive_order_matches_oracle(zk, sea):
         eh, ph, hist = o.step_ifab2(eh, ph, 0.02, hist)
     ge, gp = s.get_state()
     assert np.linalg.norm(ge - o.physical(eh)) / np.linalg.norm(o.physical(eh)) < 1e-10
+
+
+def test_ifrk4_with_adaptive_order_matches_oracle(zk, sea):
+    # as for IF-AB2: every order meets the tolerance, so the first check switches 6 -> 2 and the
+    # run is the order-2 IF-RK4 run of the oracle
+    s = zk.Zakharov(N, N, L, L, H, M=6, eps=1.0, precision=zk.ZK_F64)
+    zk.zk_set_options(s.ctx, eps=1.0, integrator=zk.ZK_IFRK4)
+    s.set_state(sea[0].astype(np.float64), sea[1].astype(np.float64))
+    zk.zk_set_adaptive_order(s.ctx, 2, 1e30, 100)
+    s.step(0.02, 10)
+    assert zk.zk_adaptive_status(s.ctx)["order"] == 2
+    o = Oracle(Grid(N, N, L, L, H), 2, eps=1.0)
+    eh, ph = o.spectrum(sea[0].astype(np.float64)), o.spectrum(sea[1].astype(np.float64))
+    for _ in range(10):
+        eh, ph = o.step_ifrk4(eh, ph, 0.02)
+    ge, gp = s.get_state()
+    assert np.linalg.norm(ge - o.physical(eh)) / np.linalg.norm(o.physical(eh)) < 1e-10
+    assert np.linalg.norm(gp - o.physical(ph)) / np.linalg.norm(o.physical(ph)) < 1e-10

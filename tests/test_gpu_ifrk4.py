@@ -51,3 +51,20 @@ def test_ifrk4_eps0_exact_linear_flow(zk):
     we, wp = o.linear_propagate(o.spectrum(e), o.spectrum(p), 3.0)
     ge, gp = s.get_state()
     assert rel(ge, o.physical(we)) < 1e-12 and rel(gp, o.physical(wp)) < 1e-12
+
+
+def test_ifrk4_config1_fp64_200_steps(zk):
+    """Config 1 (64^2, L = 100 m, h = 20 m, M = 3, seed 1, eps = 1, dt = 0.02 s, filter on):
+    200 IF-RK4 steps in FP64 against the oracle, the bar of the RK4 config-1 run (1e-10), and
+    the Hamiltonian at the end to 1e-12."""
+    e, p, _ = seas.jonswap_sea(64, 64, 100.0, 100.0, 20.0, 1.0, 8.0, 1)
+    o = Oracle(Grid(64, 64, 100.0, 100.0, 20.0), 3)
+    oe, op = run(o, e, p, 0.02, 200, integrator="ifrk4")
+    s = zk.Zakharov(64, 64, 100.0, 100.0, 20.0, M=3, precision=zk.ZK_F64)
+    zk.zk_set_options(s.ctx, eps=1.0, integrator=zk.ZK_IFRK4)
+    s.set_state(e, p)
+    s.step(0.02, 200)
+    ge, gp = s.get_state()
+    assert rel(ge, oe) < 1e-10 and rel(gp, op) < 1e-10
+    H = o.energy(o.spectrum(oe), o.spectrum(op))[0]
+    assert abs(s.energy()[0] - H) / H < 1e-12
