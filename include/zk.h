@@ -54,7 +54,7 @@ enum { ZK_RK4 = 0, ZK_IFRK4 = 1, ZK_IFAB2 = 2 };   /* time integrators */
 
 typedef struct {
     double eps;        /* nonlinear-amplitude parameter of Eqs. 9-11, in [0, 1]; default 1 */
-    int integrator;    /* ZK_RK4 (default), ZK_IFAB2 (Sec. 3.4, Eqs. 15-16) or ZK_IFRK4 */
+    int integrator;    /* ZK_RK4 (default), ZK_IFRK4 (RK4 on the rotation of Eq. 14) or ZK_IFAB2 (Sec. 3.4, Eqs. 15-16) */
     int taper;         /* 1 (default): taper exp[-(|k|/kc)^8] on nonlinear products (Sec. 6.1) */
     int filter;        /* 1 (default): state filter A(k) of Eq. 17 once per step */
     void *stream;      /* cudaStream_t for all launches; NULL = legacy default stream */
