@@ -187,6 +187,20 @@ class Clocks:
                 "samples": len(rows)}
 
 
+def host_cpu():
+    """The host's CPU model and logical core count (recorded beside the oracle timing)."""
+    model = "unknown"
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"cpu_model": model, "host_logical_cores": os.cpu_count()}
+
+
 def cpu_baseline_rhs(eta, psi):
     """One oracle right-hand side on the full workload; returns (seconds, steps/s)."""
     from oracle import Grid, Oracle
@@ -228,7 +242,8 @@ def reference_arm(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 4000.0 * tot / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": WORKLOAD.replace("FP32", "FP64 oracle"), "grid": 2048, "M": 5},
-        "cpu_baseline": {"value": value, "unit": "steps/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "steps/s", "cores": 1, "kind": "oracle", "sample": sample,
+                         **host_cpu()},
         "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -851,7 +866,7 @@ def main():
         sec, sps = cpu_baseline_rhs(eta, psi)
         cpu = {"value": sps, "unit": "steps/s", "cores": 1, "kind": "oracle",
                "sample": f"one right-hand-side evaluation of the full workload ({sec:.1f} s, FP64 numpy, "
-                         f"one thread) scaled x4 to one RK4 step"}
+                         f"one thread) scaled x4 to one RK4 step", **host_cpu()}
 
     if rank == 0:
         line = {
