@@ -10,9 +10,10 @@
 // one real 16 x 16 x 8 product (mma.sync m16n8k16, FP32 accumulation) per
 // group of 8 blocks. Each FP32 operand v is split into a 16-bit high part
 // h = rn(v) and low part l = rn(v - h), and the product takes the three terms
-// h h' + h l' + l h'; the dropped l l' term and the rounding of l are at the
-// 2^-22 level (relative to the operands) for FP16 parts and at 2^-18 for BF16
-// parts. Two forms:
+// h h' + h l' + l h'. With u the unit roundoff of the 16-bit format (2^-11 for
+// FP16, 2^-8 for BF16), the dropped l l' term and the rounding of l are each at
+// most u^2 of the operands: 2^-22 for FP16 parts, 2^-16 for BF16 parts (less on
+// average). Two forms:
 //   SPLIT_BF16: BF16 parts (FP32 exponent range, 8-bit significands);
 //   SPLIT_FP16: FP16 parts (11-bit significands). Every block (a GEMM column)
 //     is first scaled by a power of two that puts its largest component in
