@@ -57,7 +57,29 @@ __global__ void __launch_bounds__(kRowMaxThreads) row2_kernel(const RowArgs<T> a
     cx<T>* out0 = a.out0 + (long long)blockIdx.y * a.tcol;
     cx<T>* out1 = a.out1 ? a.out1 + (long long)blockIdx.y * a.tcol : nullptr;
 
+    // the series accumulator row is read by rounds r >= 3 and by the final round when M >= 3
+    const bool reads_acc = a.kind == 0 ? a.r >= 3 : a.M >= 3;
     for (int zp = blockIdx.x; zp < a.npz; zp += gridDim.x) {
+        // Ask L2 for this block's next row now: its input lines (HX contiguous values per field)
+        // and accumulator row then arrive while the current row is transformed. Sizes and
+        // addresses are multiples of 16 bytes (HX, the field stride and NPX are even).
+        const int zn = zp + gridDim.x;
+        if (zn < a.npz && threadIdx.x <= 2 * a.nlines) {
+            const void* src = nullptr;
+            unsigned bytes = 0;
+            if (threadIdx.x < 2 * a.nlines) {
+                const int l = threadIdx.x >> 1;
+                const int f = (threadIdx.x & 1) ? a.fb[l] : a.fa[l];
+                if (f >= 0) {
+                    src = colbase + (long long)f * a.fstride + (long long)zn * HX;
+                    bytes = (unsigned)(HX * sizeof(cx<T>));
+                }
+            } else if (reads_acc) {
+                src = acc + (long long)zn * NPX;
+                bytes = (unsigned)(NPX * sizeof(TA));
+            }
+            if (src) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+        }
         // Phase A: Hermitian packing of two real fields fused into the first DIF stage.
         for (int l = g; l < nloop; l += ngroups) {
             cx<T>* lb = lines + (size_t)l * LS;
@@ -296,6 +318,25 @@ col2_kernel(const ColArgs<T> a, const cx<T>* __restrict__ tw) {
     constexpr int PER = col_stride(2 * LS);
     cx<T>* l0 = sm + (size_t)g * PER;
     cx<T>* l1 = l0 + LS;
+    // The epilogue's state rows were written by the previous stage long before and come from
+    // DRAM: request this tile's rows into L2 now, so that the fetch overlaps the tile load and
+    // the two transforms (one prefetch per 32-byte sector, the addresses the epilogue reads).
+    {
+        const cx<T>* pf[6] = {a.s_eta, a.s_psi, nullptr, nullptr, nullptr, nullptr};
+        int npf = 2;
+        if (a.mode >= FIN_RK1 && a.mode <= FIN_RK4) {
+            pf[npf++] = a.y_eta;
+            pf[npf++] = a.y_psi;
+            if (a.mode != FIN_RK1) { pf[npf++] = a.ka_eta; pf[npf++] = a.ka_psi; }
+        }
+        constexpr int PER_SECTOR = 32 / (int)sizeof(cx<T>) > 0 ? 32 / (int)sizeof(cx<T>) : 1;
+        for (int i = threadIdx.x; i < NZ * npf; i += blockDim.x) {
+            const int q = i / NZ, ic = i - q * NZ;
+            const cx<T>* row = pf[q] + os + (long long)ic * a.hx + c0;
+            for (int cg = 0; cg < CB && c0 + cg < a.hx; cg += PER_SECTOR)
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(row + cg));
+        }
+    }
     for (int i = threadIdx.x; i < NPZ * CB; i += blockDim.x) {
         const int z = i / CB, cg = i - z * CB;
         const int col = c0 + cg;
