@@ -63,8 +63,10 @@ __global__ void __launch_bounds__(kRowMaxThreads) row2_kernel(const RowArgs<T> a
         // Ask L2 for this block's next row now: its input lines (HX contiguous values per field)
         // and accumulator row then arrive while the current row is transformed. Sizes and
         // addresses are multiples of 16 bytes (HX, the field stride and NPX are even).
+        // Grids below 1024 points per axis keep their fields in L2 and would only pay the
+        // instructions.
         const int zn = zp + gridDim.x;
-        if (zn < a.npz && threadIdx.x <= 2 * a.nlines) {
+        if (NPX >= 1536 && zn < a.npz && threadIdx.x <= 2 * a.nlines) {
             const void* src = nullptr;
             unsigned bytes = 0;
             if (threadIdx.x < 2 * a.nlines) {
@@ -321,7 +323,8 @@ col2_kernel(const ColArgs<T> a, const cx<T>* __restrict__ tw) {
     // The epilogue's state rows were written by the previous stage long before and come from
     // DRAM: request this tile's rows into L2 now, so that the fetch overlaps the tile load and
     // the two transforms (one prefetch per 32-byte sector, the addresses the epilogue reads).
-    {
+    // Grids below 1024 points per axis keep their state in L2: no prefetch there.
+    if constexpr (NPZ >= 1536) {
         const cx<T>* pf[6] = {a.s_eta, a.s_psi, nullptr, nullptr, nullptr, nullptr};
         int npf = 2;
         if (a.mode >= FIN_RK1 && a.mode <= FIN_RK4) {
