@@ -36,3 +36,13 @@ def test_host_cpu_fields():
 def test_job_rate_counts_every_rank():
     assert bench.job_rate(10, 1, 1000.0) == 10.0
     assert bench.job_rate(10, 4, 2000.0) == 20.0
+
+
+def test_reference_arm_other_ranks_exit_without_work():
+    """Under torchrun with N > 1 only rank 0 times the oracle; the other ranks print nothing
+    and exit 0."""
+    import subprocess
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2",
+                        "--steps", "1", "--warmup", "0"], env=env, capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and r.stdout.strip() == ""
