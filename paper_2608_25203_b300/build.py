@@ -14,7 +14,9 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libzk.so")
-SOURCES = [os.path.join(HERE, "csrc", f) for f in ("zk_api.cu", "zk_static.cu", "zk_net.cu")]
+SOURCES = [os.path.join(HERE, "csrc", f) for f in (
+    "zk_api.cu", "zk_static.cu", "zk_net.cu", "zk_launch_common.cu",
+    "zk_launch_row_f32.cu", "zk_launch_row_f64.cu", "zk_launch_col_f32.cu", "zk_launch_col_f64.cu")]
 DEPS = sorted(os.path.join(HERE, "csrc", f) for f in os.listdir(os.path.join(HERE, "csrc"))
               if f.endswith((".cu", ".cuh", ".h"))) + [os.path.join(ROOT, "include", "zk.h")]
 

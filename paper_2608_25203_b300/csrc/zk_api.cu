@@ -20,6 +20,7 @@
 
 #include "../../include/zk.h"
 #include "zk_kernels2.cuh"
+#include "zk_launch.h"
 #include "zk_net_internal.h"
 
 using namespace zk;
@@ -27,61 +28,6 @@ using namespace zk;
 namespace {
 
 constexpr int kIoElem = 8;  // bytes per staging element (fits f32 and f64)
-
-// columns per column-kernel block: 4 for wide line groups, else enough for 128 (FP32) / 64 (FP64) threads
-template <int NPZ, int ES, int V = 0> constexpr int col_cb() {
-    return IPlan<NPZ, V>::TL >= 64 ? 4 : ((ES == 8 ? 128 : 64) / IPlan<NPZ, V>::TL);
-}
-// autotuner choice ci of columns per block: 0 = half, 1 = default, 2 = double
-template <int NPZ, int ES, int V> constexpr int col_cb_pick(int ci) {
-    return ci == 0 ? (col_cb<NPZ, ES, V>() > 1 ? col_cb<NPZ, ES, V>() / 2 : 1)
-                   : (ci == 2 ? 2 * col_cb<NPZ, ES, V>() : col_cb<NPZ, ES, V>());
-}
-
-// Resident blocks per SM of a kernel shape, and the SM count (cached per shape).
-std::mutex g_occ_mu;
-std::unordered_map<std::string, std::pair<int, int>> g_occ;
-void occupancy(const void* fn, int threads, size_t smem, int* per_sm, int* sms) {
-    char key[96];
-    snprintf(key, sizeof(key), "%p/%d/%zu", fn, threads, smem);
-    {
-        std::lock_guard<std::mutex> lk(g_occ_mu);
-        auto it = g_occ.find(key);
-        if (it != g_occ.end()) { *per_sm = it->second.first; *sms = it->second.second; return; }
-    }
-    int dev = 0, n = 0, nb = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, smem);
-    *per_sm = std::max(1, nb);
-    *sms = std::max(1, n);
-    std::lock_guard<std::mutex> lk(g_occ_mu);
-    g_occ[key] = {*per_sm, *sms};
-}
-
-// Largest dynamic shared memory a block may opt in to on this device.
-int smem_optin() {
-    static int v = -1;
-    if (v < 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    }
-    return v;
-}
-
-std::mutex g_attr_mu;
-std::unordered_map<const void*, int> g_attr;
-
-cudaError_t ensure_smem(const void* fn, size_t bytes) {
-    if (bytes <= 48 * 1024) return cudaSuccess;
-    std::lock_guard<std::mutex> lk(g_attr_mu);
-    auto it = g_attr.find(fn);
-    if (it != g_attr.end() && it->second >= (int)bytes) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e == cudaSuccess) g_attr[fn] = (int)bytes;
-    return e;
-}
 
 bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
@@ -204,186 +150,6 @@ void make_twiddles(int n, std::vector<cx<T>>& out) {
     for (int t = 0; t < n; ++t) {
         const double ang = -2.0 * M_PI * (double)t / (double)n;
         out[t] = mk<T>((T)std::cos(ang), (T)std::sin(ang));
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Launch helpers dispatched on the compile-time line lengths.
-// ---------------------------------------------------------------------------
-template <typename T, int NPX, int V, typename TA = T, int DIV = 3>
-cudaError_t launch_row_t(const RowArgs<T>& a, const cx<T>* tw, int npz, cudaStream_t s) {
-    constexpr int TL = IPlan<NPX, V>::TL;
-    // narrow groups: one line per group, rounded to whole warps; wide groups:
-    // at most 1024 threads, lines beyond that taken in waves
-    int nl = a.nlines, groups;
-    if constexpr (TL < 32) { constexpr int per = 32 / TL; nl = (nl + per - 1) / per * per; groups = nl; }
-    else groups = std::min(nl, std::max(1, kRowMaxThreads / TL));
-    const int threads = groups * TL;
-    const size_t smem = (size_t)nl * line_stride(NPX) * sizeof(cx<T>);
-    if (threads > 1024 || smem > (size_t)smem_optin()) return cudaErrorInvalidConfiguration;
-    const void* fn = (const void*)row2_kernel<T, NPX, V, TA, DIV>;
-    cudaError_t e = ensure_smem(fn, smem);
-    if (e != cudaSuccess) return e;
-    RowArgs<T> b = a;
-    b.npz = npz;
-    // persistent over rows: the resident blocks (capped at a.occ per SM when
-    // set) shared among the a.nb tiles of the launch
-    int per_sm = 1, sms = 1;
-    occupancy(fn, threads, smem, &per_sm, &sms);
-    if (a.occ > 0) per_sm = std::min(per_sm, a.occ);
-    const int nb = std::max(1, a.nb);
-    const int gx = std::max(1, std::min(npz, (per_sm * sms + nb - 1) / nb));
-    row2_kernel<T, NPX, V, TA, DIV><<<dim3(gx, nb), threads, smem, s>>>(b, tw);
-    return cudaGetLastError();
-}
-
-template <typename T>
-cudaError_t launch_row(int npx, int v, const RowArgs<T>& a, const cx<T>* tw, int npz, cudaStream_t s) {
-    if (v == SPLIT_BF16 || v == SPLIT_FP16) {   // FP32 3/2-rule plans of the long lines only
-        if constexpr (sizeof(T) == 4) {
-            if (a.pad3 || a.acc64) return cudaErrorInvalidValue;
-            switch (npx * 4 + v) {
-            case 1536 * 4 + SPLIT_BF16: return launch_row_t<T, 1536, SPLIT_BF16>(a, tw, npz, s);
-            case 3072 * 4 + SPLIT_BF16: return launch_row_t<T, 3072, SPLIT_BF16>(a, tw, npz, s);
-            case 1536 * 4 + SPLIT_FP16: return launch_row_t<T, 1536, SPLIT_FP16>(a, tw, npz, s);
-            case 3072 * 4 + SPLIT_FP16: return launch_row_t<T, 3072, SPLIT_FP16>(a, tw, npz, s);
-            default: break;
-            }
-        }
-        return cudaErrorInvalidValue;
-    }
-    if constexpr (sizeof(T) == 4) {
-        if (a.pad3) {    // 3N padding: FP32, default plans and sums
-            switch (npx) {
-            case 48: return launch_row_t<T, 48, 0, T, 6>(a, tw, npz, s);
-            case 96: return launch_row_t<T, 96, 0, T, 6>(a, tw, npz, s);
-            case 192: return launch_row_t<T, 192, 0, T, 6>(a, tw, npz, s);
-            case 384: return launch_row_t<T, 384, 0, T, 6>(a, tw, npz, s);
-            case 768: return launch_row_t<T, 768, 0, T, 6>(a, tw, npz, s);
-            case 1536: return launch_row_t<T, 1536, 0, T, 6>(a, tw, npz, s);
-            case 3072: return launch_row_t<T, 3072, 0, T, 6>(a, tw, npz, s);
-            default: return cudaErrorInvalidValue;
-            }
-        }
-        if (a.acc64) {   // FP64 series sums: default plans only
-            switch (npx) {
-            case 24: return launch_row_t<T, 24, 0, double>(a, tw, npz, s);
-            case 48: return launch_row_t<T, 48, 0, double>(a, tw, npz, s);
-            case 96: return launch_row_t<T, 96, 0, double>(a, tw, npz, s);
-            case 192: return launch_row_t<T, 192, 0, double>(a, tw, npz, s);
-            case 384: return launch_row_t<T, 384, 0, double>(a, tw, npz, s);
-            case 768: return launch_row_t<T, 768, 0, double>(a, tw, npz, s);
-            case 1536: return launch_row_t<T, 1536, 0, double>(a, tw, npz, s);
-            case 3072: return launch_row_t<T, 3072, 0, double>(a, tw, npz, s);
-            default: return cudaErrorInvalidValue;
-            }
-        }
-        if (v == 1) {
-            switch (npx) {
-            case 768: return launch_row_t<T, 768, 1>(a, tw, npz, s);
-            case 1536: return launch_row_t<T, 1536, 1>(a, tw, npz, s);
-            case 3072: return launch_row_t<T, 3072, 1>(a, tw, npz, s);
-            default: break;
-            }
-        }
-    }
-    switch (npx) {
-    case 24: return launch_row_t<T, 24, 0>(a, tw, npz, s);
-    case 48: return launch_row_t<T, 48, 0>(a, tw, npz, s);
-    case 96: return launch_row_t<T, 96, 0>(a, tw, npz, s);
-    case 192: return launch_row_t<T, 192, 0>(a, tw, npz, s);
-    case 384: return launch_row_t<T, 384, 0>(a, tw, npz, s);
-    case 768: return launch_row_t<T, 768, 0>(a, tw, npz, s);
-    case 1536: return launch_row_t<T, 1536, 0>(a, tw, npz, s);
-    case 3072: if constexpr (sizeof(T) == 4) return launch_row_t<T, 3072, 0>(a, tw, npz, s); else return cudaErrorInvalidValue;
-    default: return cudaErrorInvalidValue;
-    }
-}
-
-template <typename T, int NPZ, int CB, int V, int DIV = 3>
-cudaError_t launch_col_t(const ColArgs<T>& a, const cx<T>* tw, cudaStream_t s, int* nblocks) {
-    constexpr int TL = IPlan<NPZ, V>::TL;
-    constexpr int NZ = 2 * NPZ / DIV;
-    constexpr int LS = line_stride(NPZ);
-    const int threads = CB * TL < 32 ? 32 : CB * TL;
-    const int groups = threads / TL;
-    const size_t per = (a.kind == COL_FINAL) ? (size_t)col_stride(2 * LS) : (size_t)col_stride(LS + NZ);
-    const size_t smem = (size_t)groups * per * sizeof(cx<T>);
-    if (threads > 1024 || smem > (size_t)smem_optin()) return cudaErrorInvalidConfiguration;
-    const int grid = (a.hx + CB - 1) / CB;
-    if (nblocks) *nblocks = grid;
-    cudaError_t e = ensure_smem((const void*)col2_kernel<T, NPZ, CB, V, DIV>, smem);
-    if (e != cudaSuccess) return e;
-    col2_kernel<T, NPZ, CB, V, DIV><<<dim3(grid, std::max(1, a.nb)), threads, smem, s>>>(a, tw);
-    return cudaGetLastError();
-}
-
-// Columns-per-block choice ci (0 / 1 / 2 = half / default / double) is tuned
-// for FP32 lines of 192 and longer; everything else runs the default.
-template <typename T, int NPZ, int V>
-cudaError_t launch_col_v(int ci, const ColArgs<T>& a, const cx<T>* tw, cudaStream_t s, int* nblocks) {
-    constexpr int ES = (int)sizeof(cx<T>);
-    if constexpr (ES == 8 && NPZ >= 192) {
-        if (ci == 0) return launch_col_t<T, NPZ, col_cb_pick<NPZ, ES, V>(0), V>(a, tw, s, nblocks);
-        if (ci == 2) return launch_col_t<T, NPZ, col_cb_pick<NPZ, ES, V>(2), V>(a, tw, s, nblocks);
-    }
-    return launch_col_t<T, NPZ, col_cb<NPZ, ES, V>(), V>(a, tw, s, nblocks);
-}
-
-template <typename T>
-cudaError_t launch_col(int npz, int v, int ci, const ColArgs<T>& a, const cx<T>* tw, cudaStream_t s,
-                       int* nblocks = nullptr) {
-    if (v == SPLIT_BF16 || v == SPLIT_FP16) {   // default blocking; FP32 3/2-rule plans of the long lines
-        if constexpr (sizeof(T) == 4) {
-            constexpr int ES = (int)sizeof(cx<T>);
-            if (a.pad3) return cudaErrorInvalidValue;
-            switch (npz * 4 + v) {
-            case 1536 * 4 + SPLIT_BF16:
-                return launch_col_t<T, 1536, col_cb<1536, ES, SPLIT_BF16>(), SPLIT_BF16>(a, tw, s, nblocks);
-            case 3072 * 4 + SPLIT_BF16:
-                return launch_col_t<T, 3072, col_cb<3072, ES, SPLIT_BF16>(), SPLIT_BF16>(a, tw, s, nblocks);
-            case 1536 * 4 + SPLIT_FP16:
-                return launch_col_t<T, 1536, col_cb<1536, ES, SPLIT_FP16>(), SPLIT_FP16>(a, tw, s, nblocks);
-            case 3072 * 4 + SPLIT_FP16:
-                return launch_col_t<T, 3072, col_cb<3072, ES, SPLIT_FP16>(), SPLIT_FP16>(a, tw, s, nblocks);
-            default: break;
-            }
-        }
-        return cudaErrorInvalidValue;
-    }
-    if constexpr (sizeof(T) == 4) {
-        if (a.pad3) {    // 3N padding: FP32, default plans and blocking
-            constexpr int ES = (int)sizeof(cx<T>);
-            switch (npz) {
-            case 48: return launch_col_t<T, 48, col_cb<48, ES>(), 0, 6>(a, tw, s, nblocks);
-            case 96: return launch_col_t<T, 96, col_cb<96, ES>(), 0, 6>(a, tw, s, nblocks);
-            case 192: return launch_col_t<T, 192, col_cb<192, ES>(), 0, 6>(a, tw, s, nblocks);
-            case 384: return launch_col_t<T, 384, col_cb<384, ES>(), 0, 6>(a, tw, s, nblocks);
-            case 768: return launch_col_t<T, 768, col_cb<768, ES>(), 0, 6>(a, tw, s, nblocks);
-            case 1536: return launch_col_t<T, 1536, col_cb<1536, ES>(), 0, 6>(a, tw, s, nblocks);
-            case 3072: return launch_col_t<T, 3072, col_cb<3072, ES>(), 0, 6>(a, tw, s, nblocks);
-            default: return cudaErrorInvalidValue;
-            }
-        }
-        if (v == 1) {
-            switch (npz) {
-            case 768: return launch_col_v<T, 768, 1>(ci, a, tw, s, nblocks);
-            case 1536: return launch_col_v<T, 1536, 1>(ci, a, tw, s, nblocks);
-            case 3072: return launch_col_v<T, 3072, 1>(ci, a, tw, s, nblocks);
-            default: break;
-            }
-        }
-    }
-    switch (npz) {
-    case 24: return launch_col_v<T, 24, 0>(ci, a, tw, s, nblocks);
-    case 48: return launch_col_v<T, 48, 0>(ci, a, tw, s, nblocks);
-    case 96: return launch_col_v<T, 96, 0>(ci, a, tw, s, nblocks);
-    case 192: return launch_col_v<T, 192, 0>(ci, a, tw, s, nblocks);
-    case 384: return launch_col_v<T, 384, 0>(ci, a, tw, s, nblocks);
-    case 768: return launch_col_v<T, 768, 0>(ci, a, tw, s, nblocks);
-    case 1536: return launch_col_v<T, 1536, 0>(ci, a, tw, s, nblocks);
-    case 3072: if constexpr (sizeof(T) == 4) return launch_col_v<T, 3072, 0>(ci, a, tw, s, nblocks); else return cudaErrorInvalidValue;
-    default: return cudaErrorInvalidValue;
     }
 }
 

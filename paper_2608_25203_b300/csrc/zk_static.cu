@@ -18,6 +18,8 @@
 #include <cstring>
 #include <mutex>
 
+#include <cuda.h>
+
 #include "../../include/zk.h"
 #include "zk_kernels2.cuh"
 
@@ -28,27 +30,76 @@ static __device__ __align__(256) unsigned char zk_static_scratch[ZK_STATIC_SCRAT
 
 namespace {
 
-constexpr int kMaxDevices = 64;
+// Host code cannot use the array's name as a device address: the address is
+// looked up with cudaGetSymbolAddress in the calling thread's current context
+// and cached under that context's unique id (cuCtxGetId; ids are never reused
+// within a process). A cudaDeviceReset, or a caller that makes another driver
+// context current on the same device, therefore gets a fresh lookup instead of
+// an address from a context that no longer holds the array. Where the driver
+// entry points cannot be resolved, every call looks the address up.
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+constexpr int kMaxContexts = 64;
 std::mutex g_mu;
-void* g_scratch[kMaxDevices] = {};
+bool g_resolved = false;
+CtxGetCurrentFn g_ctx_current = nullptr;
+CtxGetIdFn g_ctx_id = nullptr;
+unsigned long long g_ids[kMaxContexts] = {};
+void* g_addr[kMaxContexts] = {};
+int g_n = 0, g_next = 0;
 
-// Host code cannot use the array's name as a device address: fetch it once per
-// device, with that device current.
-zk_status scratch_address(void** out) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return ZK_ECUDA;
-    if (dev < 0 || dev >= kMaxDevices) return ZK_EUNSUPPORTED;
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch[dev]) {
-        void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, zk_static_scratch);
-        if (e != cudaSuccess || p == nullptr) {
-            cudaGetLastError();
-            return ZK_ECUDA;
-        }
-        g_scratch[dev] = p;
+void resolve_driver_entry_points() {
+    if (g_resolved) return;
+    g_resolved = true;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+        g_ctx_current = reinterpret_cast<CtxGetCurrentFn>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+        g_ctx_id = reinterpret_cast<CtxGetIdFn>(f);
+    cudaGetLastError();
+}
+
+// Unique id of the current context; false if there is none or it cannot be read.
+bool current_context_id(unsigned long long* id) {
+    if (!g_ctx_current || !g_ctx_id) return false;
+    CUcontext ctx = nullptr;
+    if (g_ctx_current(&ctx) != CUDA_SUCCESS || ctx == nullptr) return false;
+    return g_ctx_id(ctx, id) == CUDA_SUCCESS;
+}
+
+zk_status lookup_symbol(void** out) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, zk_static_scratch);
+    if (e != cudaSuccess || p == nullptr) {
+        cudaGetLastError();
+        return ZK_ECUDA;
     }
-    *out = g_scratch[dev];
+    *out = p;
+    return ZK_OK;
+}
+
+zk_status scratch_address(void** out) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    resolve_driver_entry_points();
+    unsigned long long id = 0;
+    if (current_context_id(&id)) {
+        for (int i = 0; i < g_n; ++i)
+            if (g_ids[i] == id) { *out = g_addr[i]; return ZK_OK; }
+    }
+    // first call in this context (the lookup also makes the runtime's context current)
+    void* p = nullptr;
+    const zk_status st = lookup_symbol(&p);
+    if (st != ZK_OK) return st;
+    if (current_context_id(&id)) {
+        const int slot = g_n < kMaxContexts ? g_n++ : (g_next++ % kMaxContexts);
+        g_ids[slot] = id;
+        g_addr[slot] = p;
+    }
+    *out = p;
     return ZK_OK;
 }
 
