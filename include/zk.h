@@ -210,11 +210,12 @@ zk_status zk_profile_step(zk_ctx *ctx, double dt, int nsteps, double *ms, int *k
  * process exits. eta, psi (inputs) and v (output) are device pointers to
  * FP32 [nz][nx] arrays owned by the caller. nx, nz: powers of two in
  * [16, 256]; 1 <= M <= ZK_MAX_ORDER; eps in [0, 1]; taper 0/1. Sizes whose
- * intermediates would not fit the array (e.g. 256 x 256 with M >= 7) are
- * rejected with ZK_EINVAL before any GPU work; 256 x 256 fits up to M = 6.
- * The work is queued on `stream` (cudaStream_t, NULL = legacy default) and
- * the call returns without waiting; synchronise before reading v.
- * The first call on each device looks up the array's device address, which
+ * intermediates would not fit the array (256 x 256 with M = 8) are rejected
+ * with ZK_EINVAL before any GPU work; 256 x 256 fits up to M = 7 and 128 x 128
+ * every M. The work is queued on `stream` (cudaStream_t, NULL = legacy default)
+ * and the call returns without waiting; synchronise before reading v.
+ * The first call in each CUDA context (per device, and again after a
+ * cudaDeviceReset) looks up the array's device address in that context, which
  * may load the library's device code; make that first call before any stream
  * capture. Every call on a device shares the array and overwrites what it
  * needs, so calls whose GPU work overlaps (other streams or host threads on

@@ -22,6 +22,8 @@ CASES = [
     (64, 64, 100.0, 100.0, 20.0, 3, 1.0, 1, 1.0, 8.0, 1),
     (128, 32, 200.0, 50.0, 15.0, 5, 0.7, 1, 1.0, 7.0, 2),
     (256, 256, 400.0, 400.0, 30.0, 6, 1.0, 0, 3.0, 10.0, 3),
+    # the fullest layout the scratch array accepts: 256 x 256 with seven terms
+    (256, 256, 400.0, 400.0, 30.0, 7, 0.5, 1, 2.0, 10.0, 4),
     (64, 64, 100.0, 100.0, 20.0, 3, 1.0, 1, 1.0, 8.0, 1),
 ]
 
