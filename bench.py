@@ -21,11 +21,14 @@ sampled during the timed region, and the FP64 oracle timed on this host.
 the same workload (rank 0 only).
 
 --workload tank: the closed 20 m x 20 m tank of the wave-propagation runtime
-comparison (Sec. 5, Table 3): 128 x 128 tank cells, reflecting walls by even
+comparison (Sec. 8, Table 3): 128 x 128 tank cells, reflecting walls by even
 extension to a 256 x 256 computational grid (Sec. 3.3), Gaussian bump at rest
-(A = 2 m at h = 20 m, A = 1 m at h = 1 m, sigma = 1 m, R = 6 m), eps = 1,
-IF-AB2 at dt = 0.01 s, orders 2 and 3, 2000 frames each. Prints one JSON line
-with ms per step for each case; the paper's RTX 4090 times are context only.
+(A = 2 m at h = 20 m, A = 1 m at h = 1 m, sigma = 1 m, R = 6 m), IF-AB2 at
+dt = 0.01 s, orders 2 and 3, 2000 frames each. The shallow case runs at the
+paper's eps = 1; the deep case diverges there (FP64 oracle, step 42), so it runs
+at the largest eps that stays finite (0.8 for order 2, 0.7 for order 3), with the
+same work per step. A case whose state is not finite reports no time and never
+sets the value. The paper's RTX 4090 times are context only.
 
 --workload batch: 96 independent JONSWAP tiles at dx = 0.78125 m (40 x 128^2,
 32 x 256^2, 16 x 512^2, 8 x 1024^2), orders cycling 3..6, Hs, h, Tp drawn per
@@ -124,19 +127,17 @@ def peaks():
         return FALLBACK_HBM, "fallback"
 
 
-def traffic_from_profiles(kernel_class):
-    """Per-launch DRAM bytes of a kernel class from the committed ncu summary, or None."""
-    p = os.path.join(ROOT, "profiles", "traffic_2048_M5.md")
-    if not os.path.exists(p):
-        return None
-    for line in open(p):
-        parts = [x.strip() for x in line.strip().strip("|").split("|")]
-        if len(parts) >= 3 and parts[0] == kernel_class:
-            try:
-                return float(parts[2])
-            except ValueError:
-                return None
-    return None
+# DRAM bytes per launch of each kernel class (dram__bytes_read.sum + dram__bytes_write.sum),
+# copied from one ncu capture of the current kernels; empty whenever the kernels have changed
+# since that capture, which makes the roofline's `traffic` null. TRAFFIC_SOURCE names it.
+TRAFFIC_NCU = {}
+TRAFFIC_SOURCE = None
+
+
+def traffic_of(kernel_class):
+    """(DRAM bytes per launch, source) of a kernel class from the recorded ncu capture, or (None, None)."""
+    t = TRAFFIC_NCU.get(kernel_class)
+    return (float(t), TRAFFIC_SOURCE) if t is not None else (None, None)
 
 
 class Clocks:
@@ -251,6 +252,19 @@ def reference_arm(args):
 
 
 TANK_PAPER_MS = {(20.0, 2): 6.352, (1.0, 2): 6.167, (20.0, 3): 13.52, (1.0, 3): 13.43}
+# The paper's deep tank (A = 2 m on h = 20 m, eps = 1) leaves the convergence range of the
+# series: the FP64 oracle goes non-finite at step 42 (order 2) and 26 (order 3), and no
+# reading of the taper, filter, padding or integrator moves that. The same bump stays finite
+# over 2000 frames at eps = 0.8 (order 2) and eps = 0.7 (order 3); eps scales coefficients
+# only, so the step's work is that of the eps = 1 setting. Those runs are timed instead.
+TANK_CASES = (  # h, A, M, eps, paper setting
+    (20.0, 2.0, 2, 0.8, False), (20.0, 2.0, 3, 0.7, False), (1.0, 1.0, 2, 1.0, True), (1.0, 1.0, 3, 1.0, True))
+
+
+def tank_value(cases):
+    """Worst per-step time over the cases whose state stayed finite (None if none did)."""
+    finite = [c["ms_per_step"] for c in cases if c["state_finite"]]
+    return max(finite) if finite else None
 
 
 def tank_arm(args):
@@ -265,33 +279,38 @@ def tank_arm(args):
     stream = torch.cuda.current_stream()
     m, L, dt, frames = 128, 20.0, 0.01, args.frames or 2000
     cases = []
-    for h, A in ((20.0, 2.0), (1.0, 1.0)):
-        for M in (2, 3):
-            eta, psi = seas.gaussian_bump(m, m, L, L, A)
-            sim = zk.Zakharov(2 * m, 2 * m, 2 * L, 2 * L, h, 9.81, M, zk.ZK_F32, eps=1.0, stream=stream.cuda_stream)
-            zk.zk_set_options(sim.ctx, eps=1.0, integrator=zk.ZK_IFAB2, stream=stream.cuda_stream)
-            zk.zk_set_state_tank(sim.ctx, eta.astype(np.float32), psi.astype(np.float32))
-            sim.step(dt, max(3, args.warmup))
-            torch.cuda.synchronize()
-            t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            t0.record(stream)
-            sim.step(dt, frames)
-            t1.record(stream)
-            torch.cuda.synchronize()
-            ms = t0.elapsed_time(t1) / frames
-            te = np.empty((m, m), np.float32)
-            tp = np.empty((m, m), np.float32)
-            zk.zk_get_state_tank(sim.ctx, te, tp)
-            cases.append({"h": h, "A": A, "M": M, "ms_per_step": ms, "paper_rtx4090_ms": TANK_PAPER_MS[(h, M)],
-                          "launches_per_step": zk.zk_launches_per_step(sim.ctx),
-                          "state_finite": bool(np.isfinite(te).all() and np.isfinite(tp).all()),
-                          "max_eta": float(np.abs(te).max())})
-            sim.close()
-    worst = max(c["ms_per_step"] for c in cases)
-    print(json.dumps({"metric": "closed-tank step time (Table 3 setting)", "value": worst, "unit": "ms/step",
-                      "higher_is_better": False, "steps": frames, "dtype": "f32", "data": "synthetic",
-                      "config": {"workload": "20 m tank, 128^2 cells, even extension to 256^2, Gaussian bump, "
-                                             "eps=1, IF-AB2 dt=0.01 s, M=2,3, h=20 m and 1 m"},
+    for h, A, M, eps, paper in TANK_CASES:
+        eta, psi = seas.gaussian_bump(m, m, L, L, A)
+        sim = zk.Zakharov(2 * m, 2 * m, 2 * L, 2 * L, h, 9.81, M, zk.ZK_F32, eps=eps, stream=stream.cuda_stream)
+        zk.zk_set_options(sim.ctx, eps=eps, integrator=zk.ZK_IFAB2, stream=stream.cuda_stream)
+        zk.zk_set_state_tank(sim.ctx, eta.astype(np.float32), psi.astype(np.float32))
+        sim.step(dt, max(3, args.warmup))
+        torch.cuda.synchronize()
+        zk.zk_set_state_tank(sim.ctx, eta.astype(np.float32), psi.astype(np.float32))
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        sim.step(dt, frames)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1) / frames
+        te = np.empty((m, m), np.float32)
+        tp = np.empty((m, m), np.float32)
+        zk.zk_get_state_tank(sim.ctx, te, tp)
+        finite = bool(np.isfinite(te).all() and np.isfinite(tp).all())
+        cases.append({"h": h, "A": A, "M": M, "eps": eps, "paper_setting": paper,
+                      "ms_per_step": ms if finite else None,
+                      "paper_rtx4090_ms": TANK_PAPER_MS[(h, M)],
+                      "launches_per_step": zk.zk_launches_per_step(sim.ctx),
+                      "state_finite": finite,
+                      "max_eta": float(np.abs(te).max()) if finite else None})
+        sim.close()
+    print(json.dumps({"metric": "closed-tank step time (Table 3 setting)", "value": tank_value(cases),
+                      "unit": "ms/step", "higher_is_better": False, "steps": frames, "dtype": "f32",
+                      "data": "synthetic",
+                      "config": {"workload": "20 m tank, 128^2 cells, even extension to 256^2, Gaussian bump "
+                                             "sigma=1 m R=6 m, IF-AB2 dt=0.01 s, M=2,3; shallow h=1 m A=1 m eps=1; "
+                                             "deep h=20 m A=2 m at eps=0.8 (M=2) / 0.7 (M=3), since eps=1 "
+                                             "diverges in the FP64 oracle"},
                       "cases": cases}), flush=True)
     return 0
 
@@ -826,9 +845,9 @@ def main():
     achieved = (dbytes / dn) / ((dms / dn) / 1e3) / 1e9
     step_bytes = sum(pbytes)
     step_ms_eager = sum(pms) / args.profile_steps
-    tr = traffic_from_profiles(dom)
+    tr, tr_src = traffic_of(dom)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": tr, "kernel": dom, "peak_source": peak_kind,
+            "traffic": tr, "traffic_source": tr_src, "kernel": dom, "peak_source": peak_kind,
             "algorithmic_bytes_per_launch": dbytes / dn, "mean_launch_ms": dms / dn,
             "launches_per_step": dn,
             "share_of_step": dms / step_ms_eager,

@@ -116,6 +116,24 @@ zk_status zk_set_state_async(zk_ctx *ctx, const void *eta, const void *psi, int 
 zk_status zk_get_state_async(zk_ctx *ctx, void *eta, void *psi, int dtype);
 zk_status zk_io_join(zk_ctx *ctx);
 
+/* Checkpoint and resume of a single context (library addition; the paper's
+ * integrator, Sec. 3.4, Eqs. 15-16, carries the previous step's nonlinear forcing
+ * F_{n-1}, so resuming from the state alone would restart with an IF-Euler step).
+ * A checkpoint holds the compact state spectra eta_hat, psi_hat and the IF-AB2
+ * history (F_{n-1} of both equations, the dt it was taken at, whether it is
+ * valid) plus the order the context steps at, in the context's precision.
+ * zk_checkpoint_size: bytes of a checkpoint of this context (header included).
+ * zk_checkpoint_save: waits for the context's stream, then copies the checkpoint
+ *   to host memory `buf` (caller-owned, at least zk_checkpoint_size bytes).
+ * zk_checkpoint_load: restores a checkpoint into a context created with the same
+ *   grid, order, precision and padding (the header is checked: ZK_EINVAL on a
+ *   mismatch or a short buffer; ZK_ESTATE if `buf` holds no state). Options are
+ *   not part of the checkpoint. After a load, stepping continues bitwise
+ *   identically to the uninterrupted run. */
+zk_status zk_checkpoint_size(const zk_ctx *ctx, size_t *bytes);
+zk_status zk_checkpoint_save(zk_ctx *ctx, void *buf, size_t bytes);
+zk_status zk_checkpoint_load(zk_ctx *ctx, const void *buf, size_t bytes);
+
 /* Right-hand side of Eqs. 4 and 10 at the current state, as physical fields
  * [nz][nx]: d eta/dt = G(eta) psi (mean set to zero), d psi/dt. Synchronises. */
 zk_status zk_rhs(zk_ctx *ctx, void *deta_dt, void *dpsi_dt, int dtype, int on_device);

@@ -1397,6 +1397,66 @@ zk_status zk_get_state_async(zk_ctx* c, void* eta, void* psi, int dtype) {
     return ZK_OK;
 }
 
+namespace {
+struct CkptHeader {
+    char magic[8];
+    int version, nx, nz, M, m_run, prec, pad3, has_state, ab_valid, pad_;
+    double Lx, Lz, h, g, ab_dt;
+};
+constexpr char kCkptMagic[8] = {'z', 'k', 'c', 'k', 'p', 't', '0', '1'};
+size_t ckpt_compact(const zk_ctx* c) { return (size_t)c->nz * c->hx * c->csz; }
+}  // namespace
+
+zk_status zk_checkpoint_size(const zk_ctx* c, size_t* bytes) {
+    if (!c || !bytes || c->nb != 1) return ZK_EINVAL;
+    *bytes = sizeof(CkptHeader) + 4 * ckpt_compact(c);
+    return ZK_OK;
+}
+
+zk_status zk_checkpoint_save(zk_ctx* c, void* buf, size_t bytes) {
+    size_t need = 0;
+    if (!buf || zk_checkpoint_size(c, &need) != ZK_OK || bytes < need) return ZK_EINVAL;
+    if (!c->has_state) return ZK_ESTATE;
+    CkptHeader hd{};
+    std::memcpy(hd.magic, kCkptMagic, sizeof(kCkptMagic));
+    hd.version = 1; hd.nx = c->nx; hd.nz = c->nz; hd.M = c->M; hd.m_run = c->m_run; hd.prec = c->prec;
+    hd.pad3 = c->pad3 ? 1 : 0; hd.has_state = 1; hd.ab_valid = c->ab_valid ? 1 : 0;
+    hd.Lx = c->Lx; hd.Lz = c->Lz; hd.h = c->h; hd.g = c->g; hd.ab_dt = c->ab_dt;
+    cudaStream_t s = user_stream(c);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return ZK_ECUDA;
+    unsigned char* out = static_cast<unsigned char*>(buf);
+    std::memcpy(out, &hd, sizeof(hd));
+    const size_t n = ckpt_compact(c);
+    const void* src[4] = {c->y_eta, c->y_psi, c->h_eta, c->h_psi};
+    for (int i = 0; i < 4; ++i)
+        if (cudaMemcpy(out + sizeof(hd) + i * n, src[i], n, cudaMemcpyDeviceToHost) != cudaSuccess) return ZK_ECUDA;
+    return ZK_OK;
+}
+
+zk_status zk_checkpoint_load(zk_ctx* c, const void* buf, size_t bytes) {
+    size_t need = 0;
+    if (!buf || zk_checkpoint_size(c, &need) != ZK_OK || bytes < need) return ZK_EINVAL;
+    CkptHeader hd;
+    std::memcpy(&hd, buf, sizeof(hd));
+    if (std::memcmp(hd.magic, kCkptMagic, sizeof(kCkptMagic)) != 0 || hd.version != 1 || hd.nx != c->nx ||
+        hd.nz != c->nz || hd.M != c->M || hd.prec != c->prec || hd.pad3 != (c->pad3 ? 1 : 0) || hd.Lx != c->Lx ||
+        hd.Lz != c->Lz || hd.h != c->h || hd.g != c->g || hd.m_run < 1 || hd.m_run > c->M)
+        return ZK_EINVAL;
+    if (!hd.has_state) return ZK_ESTATE;
+    cudaStream_t s = user_stream(c);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return ZK_ECUDA;
+    const unsigned char* in = static_cast<const unsigned char*>(buf);
+    const size_t n = ckpt_compact(c);
+    void* dst[4] = {c->y_eta, c->y_psi, c->h_eta, c->h_psi};
+    for (int i = 0; i < 4; ++i)
+        if (cudaMemcpy(dst[i], in + sizeof(hd) + i * n, n, cudaMemcpyHostToDevice) != cudaSuccess) return ZK_ECUDA;
+    if (hd.m_run != c->m_run) { c->m_run = hd.m_run; drop_graph(c); }
+    c->has_state = true;
+    c->ab_valid = hd.ab_valid != 0;
+    c->ab_dt = hd.ab_dt;
+    return ZK_OK;
+}
+
 zk_status zk_io_join(zk_ctx* c) {
     if (!c) return ZK_EINVAL;
     if (!c->io) return ZK_OK;

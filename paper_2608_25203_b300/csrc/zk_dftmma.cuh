@@ -197,6 +197,15 @@ struct IPlanSplit {
         dit_run_blk<N, N / R1, INV, T, OFF, 8, 8>(b, tws, tid, nt);
         dit_last_blk<N, R1, INV, T>(b, tws, tid, nt, st);
     }
+    template <int TLB, bool INV, typename T, class Store>
+    static __device__ __forceinline__ void dit_wide(cx<T>* b, const cx<T>* __restrict__ tws, int tid, int bar,
+                                                    Store st) {
+        static_assert(sizeof(T) == 4, "split-precision stages are FP32 only");
+        dft8_line_blk<N, INV, PREC>(b, tid, TLB);
+        wide_sync<TLB>(bar);
+        dit_run_w<N, N / R1, TLB, INV, T, OFF, 8, 8>(b, tws, tid, bar);
+        dit_last_w<N, R1, TLB, INV, T>(b, tws, tid, st);
+    }
 };
 template <> struct IPlan<1536, SPLIT_BF16> : IPlanSplit<1536, SPLIT_BF16> {};
 template <> struct IPlan<3072, SPLIT_BF16> : IPlanSplit<3072, SPLIT_BF16> {};

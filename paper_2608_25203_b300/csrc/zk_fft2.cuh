@@ -216,6 +216,78 @@ __device__ __forceinline__ void dit_last_blk(const cx<T>* buf, const cx<T>* __re
     }
 }
 
+// ---- wide-group variants: a group of TLB threads (whole warps, compile-time
+// width, named barrier `bar`) transforms one line; TLB need not divide N/R
+// (threads past N/R idle in that stage). Used by the row kernel's forward
+// transform, where one line is shared by the threads of several line groups.
+template <int TLB>
+__device__ __forceinline__ void wide_sync(int bar) {
+    asm volatile("bar.sync %0, %1;" ::"r"(bar), "n"(TLB) : "memory");
+}
+
+template <int N, int B, int R, int TLB, bool INV, typename T, int OFF>
+__device__ __forceinline__ void dit_stage_w(cx<T>* buf, const cx<T>* __restrict__ tws, int tid) {
+    constexpr int SUB = B / R, NB = N / R;
+    constexpr int PER = (NB + TLB - 1) / TLB;
+    constexpr bool EVEN = NB % TLB == 0;
+    constexpr bool FIXED = (SUB > 1) && EVEN && (TLB % SUB == 0);
+    cx<T> wf[R > 1 ? R - 1 : 1];
+    if constexpr (FIXED) {
+#pragma unroll
+        for (int m = 1; m < R; ++m) wf[m - 1] = __ldg(&tws[OFF + (m - 1) * SUB + tid % SUB]);
+    }
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+        const int b = tid + p * TLB;
+        if (EVEN || b < NB) {
+            const int blk = b / SUB, n1 = b - blk * SUB;
+            const int base = blk * B + n1;
+            const int pb = stage_pbase<B, SUB>(blk, n1);
+            cx<T> v[R];
+#pragma unroll
+            for (int m = 0; m < R; ++m) v[m] = buf[stage_slot<B, SUB>(pb, base, m)];
+            if constexpr (SUB > 1) {
+#pragma unroll
+                for (int m = 1; m < R; ++m)
+                    v[m] = cmulc<INV>(v[m], FIXED ? wf[m - 1] : __ldg(&tws[OFF + (m - 1) * SUB + n1]));
+            }
+            SmallDFT<R, INV, T>::run(v);
+#pragma unroll
+            for (int m = 0; m < R; ++m) buf[stage_slot<B, SUB>(pb, base, m)] = v[m];
+        }
+    }
+}
+
+template <int N, int B, int TLB, bool INV, typename T, int OFF, int R, int... Rest>
+__device__ __forceinline__ void dit_run_w(cx<T>* buf, const cx<T>* __restrict__ tws, int tid, int bar) {
+    if constexpr (sizeof...(Rest) > 0)
+        dit_run_w<N, B / R, TLB, INV, T, OFF + (R - 1) * (B / R), Rest...>(buf, tws, tid, bar);
+    dit_stage_w<N, B, R, TLB, INV, T, OFF>(buf, tws, tid);
+    wide_sync<TLB>(bar);
+}
+
+template <int N, int R, int TLB, bool INV, typename T, class Store>
+__device__ __forceinline__ void dit_last_w(const cx<T>* buf, const cx<T>* __restrict__ tws, int tid, Store st) {
+    constexpr int SUB = N / R;
+    constexpr int PER = (SUB + TLB - 1) / TLB;
+    constexpr bool EVEN = SUB % TLB == 0;
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+        const int n1 = tid + p * TLB;
+        if (EVEN || n1 < SUB) {
+            cx<T> v[R];
+            const int pb = stage_pbase<N, SUB>(0, n1);
+#pragma unroll
+            for (int m = 0; m < R; ++m) v[m] = buf[stage_slot<N, SUB>(pb, n1, m)];
+#pragma unroll
+            for (int m = 1; m < R; ++m) v[m] = cmulc<INV>(v[m], __ldg(&tws[(m - 1) * SUB + n1]));
+            SmallDFT<R, INV, T>::run(v);
+#pragma unroll
+            for (int m = 0; m < R; ++m) st(n1 + m * SUB, v[m]);
+        }
+    }
+}
+
 // Plans for the 3/2-padded line lengths: line-group width TL and radices in
 // DIF order. The last DIF stage is radix 16 (or 8 for the smallest line):
 // its stride-16 groups land on distinct banks with the pad-per-16 layout,
@@ -249,6 +321,12 @@ template <int N, int V = 0> struct IPlan;
                                                        int nt, Store st) {                               \
             dit_run_blk<N_, N_ / R1_, INV, T, (R1_ - 1) * (N_ / R1_), __VA_ARGS__>(b, tws, tid, nt);     \
             dit_last_blk<N_, R1_, INV, T>(b, tws, tid, nt, st);                                          \
+        }                                                                                                \
+        template <int TLB, bool INV, typename T, class Store>                                            \
+        static __device__ __forceinline__ void dit_wide(cx<T>* b, const cx<T>* __restrict__ tws, int tid,\
+                                                        int bar, Store st) {                             \
+            dit_run_w<N_, N_ / R1_, TLB, INV, T, (R1_ - 1) * (N_ / R1_), __VA_ARGS__>(b, tws, tid, bar); \
+            dit_last_w<N_, R1_, TLB, INV, T>(b, tws, tid, st);                                           \
         }                                                                                                \
     };
 ZK_IPLAN(24, 0, 1, 3, 8)

@@ -21,6 +21,19 @@ template <typename T> __device__ __forceinline__ void d_sincos(T x, T* s, T* c);
 template <> __device__ __forceinline__ void d_sincos<float>(float x, float* s, float* c) { sincosf(x, s, c); }
 template <> __device__ __forceinline__ void d_sincos<double>(double x, double* s, double* c) { sincos(x, s, c); }
 
+// Taper of Sec. 6.1, exp[-(|k|/kc)^8], from u2 = |k|^2 / kc^2. FP32 contexts use the
+// hardware exponential (__expf: a few ulp near 1, far below the FP32 rounding of the
+// products it multiplies); FP64 contexts use exp.
+template <typename T> __device__ __forceinline__ T d_taper(T u2);
+template <> __device__ __forceinline__ float d_taper<float>(float u2) {
+    const float u4 = u2 * u2;
+    return __expf(-(u4 * u4));
+}
+template <> __device__ __forceinline__ double d_taper<double>(double u2) {
+    const double u4 = u2 * u2;
+    return exp(-(u4 * u4));
+}
+
 // ---------------------------------------------------------------------------
 // Row kernel: persistent over padded rows.
 // ---------------------------------------------------------------------------
@@ -34,6 +47,7 @@ template <> __device__ __forceinline__ void d_sincos<double>(double x, double* s
 #define ZK_ROW_MAX_THREADS 1024
 #endif
 constexpr int kRowMaxThreads = ZK_ROW_MAX_THREADS;
+
 
 // DIV = NPX / (nx / 2): 3 for the 3/2 rule, 6 for the 3N padding.
 template <typename T, int NPX, int V = 0, typename TA = T, int DIV = 3>
@@ -124,8 +138,11 @@ __global__ void __launch_bounds__(kRowMaxThreads) row2_kernel(const RowArgs<T> a
                 const int r = a.r;
                 const TA eta = slot(a.s_eta, p);
                 TA W = 0, Phi = 0, ep = 1;
-                for (int q = 1; q <= r; ++q) {
-                    const TA eq = ep * eta / (TA)q;
+                // unrolled over the largest order so that each 1/q is a constant (no division)
+#pragma unroll
+                for (int q = 1; q <= kMaxOrder; ++q) {
+                    if (q > r) break;
+                    const TA eq = ep * eta * (TA)(1.0 / q);
                     const TA F = slot(a.s_F0 + (r - q), p);
                     W += ep * F;
                     Phi -= eq * F;
@@ -154,9 +171,11 @@ __global__ void __launch_bounds__(kRowMaxThreads) row2_kernel(const RowArgs<T> a
                 if (M >= 2) {
                     const TA eta = slot(a.s_eta, p);
                     TA W = 0, ep = 1;
-                    for (int q = 1; q <= M; ++q) {
+#pragma unroll
+                    for (int q = 1; q <= kMaxOrder; ++q) {
+                        if (q > M) break;
                         W += ep * (TA)slot(a.s_F0 + (M - q), p);
-                        ep = ep * eta / (TA)q;
+                        ep = ep * eta * (TA)(1.0 / q);
                     }
                     Gnl = (TA)a.epsp[M - 1] * W - eps * d;
                     if (M >= 3) Gnl += accrow[p] + (TA)a.epsp[2] * g2 * g0;
@@ -169,16 +188,33 @@ __global__ void __launch_bounds__(kRowMaxThreads) row2_kernel(const RowArgs<T> a
         }
         __syncthreads();
 
-        // Phase C: forward DIT of line 0 by the whole block; keep kx < nx/2.
+        // Phase C: forward DIT of line 0; blocks of up to three line groups run it as one
+        // group of compile-time width, wider blocks with run-time strides; keep kx < nx/2.
         {
             cx<T>* o0 = out0 + (long long)zp * HX;
+            auto fwd0 = [&](auto st) {
+                if constexpr (TL >= 32) {
+                    constexpr int kBarC = 15;
+                    const int ng = blockDim.x / TL;
+                    if (ng == 3) {
+                        P::template dit_wide<3 * TL, false, T>(lines, tw, threadIdx.x, kBarC, st);
+                    } else if (ng == 2) {
+                        P::template dit_wide<2 * TL, false, T>(lines, tw, threadIdx.x, kBarC, st);
+                    } else if (ng == 1) {
+                        P::template dit_wide<TL, false, T>(lines, tw, threadIdx.x, kBarC, st);
+                    } else {
+                        P::template dit_blk<false, T>(lines, tw, threadIdx.x, blockDim.x, st);
+                    }
+                } else {
+                    P::template dit_blk<false, T>(lines, tw, threadIdx.x, blockDim.x, st);
+                }
+            };
             if (a.kind == 0) {
-                P::template dit_blk<false, T>(lines, tw, threadIdx.x, blockDim.x, [&](int k, cx<T> v) {
+                fwd0([&](int k, cx<T> v) {
                     if (k < HX) o0[k] = v;
                 });
             } else {
-                P::template dit_blk<false, T>(lines, tw, threadIdx.x, blockDim.x,
-                                              [&](int k, cx<T> v) { lines[pidx(k)] = v; });
+                fwd0([&](int k, cx<T> v) { lines[pidx(k)] = v; });
                 __syncthreads();
                 cx<T>* o1 = out1 + (long long)zp * HX;
                 for (int k = threadIdx.x; k < HX; k += blockDim.x) {
@@ -202,10 +238,44 @@ __global__ void __launch_bounds__(kRowMaxThreads) row2_kernel(const RowArgs<T> a
 // cooperative tile access on distinct 8-byte banks.
 __host__ __device__ constexpr int col_stride(int need) { return (need + 15) / 16 * 16 + 4; }
 
-template <typename T, int NPZ, int CB>
+// Dynamic shared memory of a column-kernel block with `groups` line groups: per
+// column, the line and the truncated spectrum S (spectral kinds) or two lines (final).
+template <typename T, int NPZ, int DIV>
+__host__ __device__ constexpr size_t col_smem_bytes(bool final_kind, int groups) {
+    return (size_t)groups * (final_kind ? col_stride(2 * line_stride(NPZ)) : col_stride(line_stride(NPZ) + 2 * NPZ / DIV)) *
+           sizeof(cx<T>);
+}
+
+// Cooperative load of a [NR x CB] tile (rows 0..NR-1, columns c0..c0+CB-1 of a row-major
+// [NR][hx] complex array; columns at or past hx read as zero) into shared memory at
+// sm[cg * per + slot(z)]. Each thread issues all of its loads before its first store, so
+// the tile costs about one memory round trip: the column kernels run one block per SM and
+// nothing else hides this phase.
+template <typename T, int NR, int CB, int NT, class Slot>
+__device__ __forceinline__ void col2_load_tile(const cx<T>* __restrict__ src, int hx, int c0, cx<T>* sm, int per,
+                                               Slot slot) {
+    constexpr int N = NR * CB;
+    constexpr int PERT = (N + NT - 1) / NT;
+    cx<T> v[PERT];
+#pragma unroll
+    for (int j = 0; j < PERT; ++j) {
+        const int i = threadIdx.x + j * NT;
+        const int z = i / CB, cg = i - z * CB;
+        v[j] = ((N % NT == 0 || i < N) && c0 + cg < hx) ? __ldg(src + (long long)z * hx + c0 + cg) : mk<T>(0, 0);
+    }
+#pragma unroll
+    for (int j = 0; j < PERT; ++j) {
+        const int i = threadIdx.x + j * NT;
+        const int z = i / CB, cg = i - z * CB;
+        if (N % NT == 0 || i < N) sm[(size_t)cg * per + slot(z)] = v[j];
+    }
+}
+
+template <typename T, int NPZ, int CB, int NT>
 __device__ __forceinline__ void col2_store_tile(const cx<T>* sm, int per, cx<T>* dst, int c0, int hx) {
     constexpr int N = NPZ * CB;
-    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+#pragma unroll 4
+    for (int i = threadIdx.x; i < N; i += NT) {
         const int z = i / CB, cg = i - z * CB;
         if (c0 + cg < hx) dst[(long long)z * hx + c0 + cg] = sm[(size_t)cg * per + pidx(z)];
     }
@@ -227,6 +297,7 @@ col2_kernel(const ColArgs<T> a, const cx<T>* __restrict__ tw) {
     constexpr int TL = P::TL;
     constexpr int NZ = 2 * NPZ / DIV;
     constexpr int LS = line_stride(NPZ);
+    constexpr int NT = CB * TL < 32 ? 32 : CB * TL;   // threads of the block (the launch uses exactly this)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
     const int g = threadIdx.x / TL, lt = threadIdx.x % TL;
@@ -239,6 +310,8 @@ col2_kernel(const ColArgs<T> a, const cx<T>* __restrict__ tw) {
     const long long oc = (long long)blockIdx.y * a.tcol;   // this tile's column-space fields
     const long long os = (long long)blockIdx.y * a.tst;    // this tile's compact spectra
     const T hh = a.hb ? a.hb[blockIdx.y] : a.h;
+    const T ikc2 = (T)1 / (a.kc * a.kc);                   // taper argument |k|^2 / kc^2
+    const T ihx = (T)1 / (T)a.hx, inz2 = (T)1 / (T)(NZ / 2);  // filter arguments |k_a| / kNyq_a
 
     if (a.kind == COL_FROM_STATE || a.kind == COL_PHI) {
         constexpr int PER = col_stride(LS + NZ);
@@ -248,18 +321,10 @@ col2_kernel(const ColArgs<T> a, const cx<T>* __restrict__ tw) {
         for (int src = 0; src < nsrc; ++src) {
             if (a.kind == COL_FROM_STATE) {
                 const cx<T>* st = (src == 0 ? a.st_eta : a.st_psi) + os;
-                for (int i = threadIdx.x; i < NZ * CB; i += blockDim.x) {
-                    const int z = i / CB, cg = i - z * CB;
-                    const int col = c0 + cg;
-                    sm[(size_t)cg * PER + LS + z] = col < a.hx ? st[(long long)z * a.hx + col] : mk<T>(0, 0);
-                }
+                col2_load_tile<T, NZ, CB, NT>(st, a.hx, c0, sm, PER, [](int z) { return LS + z; });
                 __syncthreads();
             } else {
-                for (int i = threadIdx.x; i < NPZ * CB; i += blockDim.x) {
-                    const int z = i / CB, cg = i - z * CB;
-                    const int col = c0 + cg;
-                    sm[(size_t)cg * PER + pidx(z)] = col < a.hx ? a.pin[oc + (long long)z * a.hx + col] : mk<T>(0, 0);
-                }
+                col2_load_tile<T, NPZ, CB, NT>(a.pin + oc, a.hx, c0, sm, PER, [](int z) { return pidx(z); });
                 __syncthreads();
                 // forward DIT: truncate to the kept modes, scale and taper into S
                 const T fs = a.fscale;
@@ -270,11 +335,7 @@ col2_kernel(const ColArgs<T> a, const cx<T>* __restrict__ tw) {
                     else return;
                     const T kz = a.kz0 * (T)mz;
                     T s = fs;
-                    if (a.taper) {
-                        const T kk2 = (kx * kx + kz * kz) / (a.kc * a.kc);
-                        const T k4 = kk2 * kk2;
-                        s *= d_exp(-(k4 * k4));
-                    }
+                    if (a.taper) s *= d_taper((kx * kx + kz * kz) * ikc2);
                     S[mz >= 0 ? mz : mz + NZ] = cscale(v, s);
                 });
                 if (lt == 0) S[NZ / 2] = mk<T>(0, 0);
@@ -293,7 +354,8 @@ col2_kernel(const ColArgs<T> a, const cx<T>* __restrict__ tw) {
                     else if (ip < NZ / 2) mz = ip;
                     else if (ip > NPZ - NZ / 2) mz = ip - NPZ;
                     else return mk<T>(0, 0);
-                    const cx<T> s = S[mz >= 0 ? mz : mz + NZ];
+                    const int iz = mz >= 0 ? mz : mz + NZ;
+                    const cx<T> s = S[iz];
                     const T kz = a.kz0 * (T)mz;
                     if (sym == SYM_ID) return cscale(s, isc);
                     if (sym == SYM_DZ) return cscale(mk<T>(-kz * s.y, kz * s.x), isc);
@@ -309,7 +371,7 @@ col2_kernel(const ColArgs<T> a, const cx<T>* __restrict__ tw) {
                 };
                 P::template dif<true, T>(line, tw, lt, bar, ld);
                 __syncthreads();
-                col2_store_tile<T, NPZ, CB>(sm, PER, a.colbase + oc + (long long)a.out_f[o] * a.fstride, c0, a.hx);
+                col2_store_tile<T, NPZ, CB, NT>(sm, PER, a.colbase + oc + (long long)a.out_f[o] * a.fstride, c0, a.hx);
                 __syncthreads();
             }
         }
@@ -340,13 +402,8 @@ col2_kernel(const ColArgs<T> a, const cx<T>* __restrict__ tw) {
                 asm volatile("prefetch.global.L2 [%0];" ::"l"(row + cg));
         }
     }
-    for (int i = threadIdx.x; i < NPZ * CB; i += blockDim.x) {
-        const int z = i / CB, cg = i - z * CB;
-        const int col = c0 + cg;
-        const bool in = col < a.hx;
-        sm[(size_t)cg * PER + pidx(z)] = in ? a.gin[oc + (long long)z * a.hx + col] : mk<T>(0, 0);
-        sm[(size_t)cg * PER + LS + pidx(z)] = in ? a.nin[oc + (long long)z * a.hx + col] : mk<T>(0, 0);
-    }
+    col2_load_tile<T, NPZ, CB, NT>(a.gin + oc, a.hx, c0, sm, PER, [](int z) { return pidx(z); });
+    col2_load_tile<T, NPZ, CB, NT>(a.nin + oc, a.hx, c0, sm, PER, [](int z) { return LS + pidx(z); });
     __syncthreads();
     P::template dit<false, T>(l0, tw, lt, bar, [&](int k, cx<T> v) { l0[pidx(k)] = v; });
     P::template dit<false, T>(l1, tw, lt, bar, [&](int k, cx<T> v) { l1[pidx(k)] = v; });
@@ -370,11 +427,7 @@ col2_kernel(const ColArgs<T> a, const cx<T>* __restrict__ tw) {
         const T kz = a.kz0 * (T)mz;
         const T k = d_sqrt(kxc * kxc + kz * kz);
         T s = a.fscale;
-        if (a.taper) {
-            const T kk = k / a.kc;
-            const T k2 = kk * kk, k4 = k2 * k2;
-            s *= d_exp(-(k4 * k4));
-        }
+        if (a.taper) s *= d_taper((kxc * kxc + kz * kz) * ikc2);
         const cx<T>* lc = sm + (size_t)cg * PER;
         cx<T> Fe = cscale(lc[pidx(ip)], s);
         const cx<T> Fp = cscale(lc[LS + pidx(ip)], s);
@@ -417,8 +470,8 @@ col2_kernel(const ColArgs<T> a, const cx<T>* __restrict__ tw) {
             cx<T> e1 = cadd(cadd(cscale(se, c), cscale(sp, G0sw)), cadd(cscale(Fse, sw), cscale(Fsp, omc_g)));
             cx<T> p1 = cadd(csub(cscale(sp, c), cscale(se, gsw)), csub(cscale(Fsp, sw), cscale(Fse, omc_G0)));
             if (a.filter) {
-                const T rx = (T)col / (T)a.hx;
-                const T rz = (T)(mz < 0 ? -mz : mz) / (T)(NZ / 2);
+                const T rx = (T)col * ihx;
+                const T rz = (T)(mz < 0 ? -mz : mz) * inz2;
                 const T A = (T)0.125 * ((T)5 + (T)4 * d_cospi(rx) - d_cospi((T)2 * rx)) *
                             ((T)0.125 * ((T)5 + (T)4 * d_cospi(rz) - d_cospi((T)2 * rz)));
                 e1 = cscale(e1, A);
@@ -470,8 +523,8 @@ col2_kernel(const ColArgs<T> a, const cx<T>* __restrict__ tw) {
             } else {
                 T A = 1;
                 if (a.filter) {
-                    const T rx = (T)col / (T)a.hx;
-                    const T rz = (T)(mz < 0 ? -mz : mz) / (T)(NZ / 2);
+                    const T rx = (T)col * ihx;
+                    const T rz = (T)(mz < 0 ? -mz : mz) * inz2;
                     A = (T)0.125 * ((T)5 + (T)4 * d_cospi(rx) - d_cospi((T)2 * rx)) *
                         ((T)0.125 * ((T)5 + (T)4 * d_cospi(rz) - d_cospi((T)2 * rz)));
                 }
@@ -500,8 +553,8 @@ col2_kernel(const ColArgs<T> a, const cx<T>* __restrict__ tw) {
             const T w = a.dt / (T)6;
             T A = 1;
             if (a.filter) {
-                const T rx = (T)col / (T)a.hx;
-                const T rz = (T)(mz < 0 ? -mz : mz) / (T)(NZ / 2);
+                const T rx = (T)col * ihx;
+                const T rz = (T)(mz < 0 ? -mz : mz) * inz2;
                 A = (T)0.125 * ((T)5 + (T)4 * d_cospi(rx) - d_cospi((T)2 * rx)) *
                     ((T)0.125 * ((T)5 + (T)4 * d_cospi(rz) - d_cospi((T)2 * rz)));
             }
@@ -589,6 +642,7 @@ __global__ void closure_combine_kernel(ColArgs<T> a, const cx<T>* __restrict__ R
                                        ClosureScales sc) {
     const int NZ = a.nz_grid, hx = a.hx;
     const long long n = (long long)NZ * hx;
+    const T ihx = (T)1 / (T)hx, inz2 = (T)1 / (T)(NZ / 2);
     for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
          idx += (long long)gridDim.x * blockDim.x) {
         const int ic = (int)(idx / hx), col = (int)(idx - (long long)ic * hx);
@@ -629,8 +683,8 @@ __global__ void closure_combine_kernel(ColArgs<T> a, const cx<T>* __restrict__ R
             const T w = a.dt / (T)6;
             T A = 1;
             if (a.filter) {
-                const T rx = (T)col / (T)a.hx;
-                const T rz = (T)(mz < 0 ? -mz : mz) / (T)(NZ / 2);
+                const T rx = (T)col * ihx;
+                const T rz = (T)(mz < 0 ? -mz : mz) * inz2;
                 A = (T)0.125 * ((T)5 + (T)4 * d_cospi(rx) - d_cospi((T)2 * rx)) *
                     ((T)0.125 * ((T)5 + (T)4 * d_cospi(rz) - d_cospi((T)2 * rz)));
             }

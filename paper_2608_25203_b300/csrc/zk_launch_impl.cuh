@@ -106,8 +106,7 @@ cudaError_t launch_col_t(const ColArgs<T>& a, const cx<T>* tw, cudaStream_t s, i
     constexpr int LS = line_stride(NPZ);
     const int threads = CB * TL < 32 ? 32 : CB * TL;
     const int groups = threads / TL;
-    const size_t per = (a.kind == COL_FINAL) ? (size_t)col_stride(2 * LS) : (size_t)col_stride(LS + NZ);
-    const size_t smem = (size_t)groups * per * sizeof(cx<T>);
+    const size_t smem = col_smem_bytes<T, NPZ, DIV>(a.kind == COL_FINAL, groups);
     if (threads > 1024 || smem > (size_t)smem_optin()) return cudaErrorInvalidConfiguration;
     const int grid = (a.hx + CB - 1) / CB;
     if (nblocks) *nblocks = grid;

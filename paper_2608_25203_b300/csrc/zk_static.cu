@@ -201,8 +201,7 @@ cudaError_t s_col(const ColArgs<float>& a, const cx<float>* tw, cudaStream_t s) 
     constexpr int NZ = 2 * NPZ / 3;
     constexpr int LS = line_stride(NPZ);
     const int threads = CB * TL < 32 ? 32 : CB * TL;
-    const size_t per = (a.kind == COL_FINAL) ? (size_t)col_stride(2 * LS) : (size_t)col_stride(LS + NZ);
-    const size_t smem = (size_t)(threads / TL) * per * sizeof(cx<float>);
+    const size_t smem = col_smem_bytes<float, NPZ, 3>(a.kind == COL_FINAL, threads / TL);
     cudaError_t e = smem_attr((const void*)col2_kernel<float, NPZ, CB>, smem);
     if (e != cudaSuccess) return e;
     col2_kernel<float, NPZ, CB><<<(a.hx + CB - 1) / CB, threads, smem, s>>>(a, tw);

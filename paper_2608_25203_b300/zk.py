@@ -25,7 +25,8 @@ ZK_DFT_F32, ZK_DFT_BF16X3, ZK_DFT_FP16X3 = 0, 1, 2
 
 # every symbol include/zk.h declares
 EXPORTS = [
-    "zk_create", "zk_create_ex", "zk_set_state_async", "zk_get_state_async", "zk_io_join", "zk_destroy", "zk_set_options", "zk_get_options", "zk_set_state", "zk_get_state",
+    "zk_create", "zk_create_ex", "zk_set_state_async", "zk_get_state_async", "zk_io_join",
+    "zk_checkpoint_size", "zk_checkpoint_save", "zk_checkpoint_load", "zk_destroy", "zk_set_options", "zk_get_options", "zk_set_state", "zk_get_state",
     "zk_rhs", "zk_dno", "zk_step", "zk_energy", "zk_sync", "zk_device_bytes",
     "zk_launches_per_step", "zk_profile_step", "zk_dno_static", "zk_dno_inverse", "zk_relax",
     "zk_set_state_tank", "zk_get_state_tank", "zk_set_series_fp64", "zk_set_dft_precision",
@@ -77,6 +78,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "zk_set_state_async": ([vp, vp, vp, i], i),
         "zk_get_state_async": ([vp, vp, vp, i], i),
         "zk_io_join": ([vp], i),
+        "zk_checkpoint_size": ([vp, ctypes.POINTER(ctypes.c_size_t)], i),
+        "zk_checkpoint_save": ([vp, vp, ctypes.c_size_t], i),
+        "zk_checkpoint_load": ([vp, vp, ctypes.c_size_t], i),
         "zk_destroy": ([vp], None),
         "zk_set_options": ([vp, ctypes.POINTER(ZkOptions)], i),
         "zk_get_options": ([vp, ctypes.POINTER(ZkOptions)], i),
@@ -233,6 +237,21 @@ def zk_device_bytes(ctx):
     b = ctypes.c_size_t()
     _check("zk_device_bytes", load().zk_device_bytes(ctx, ctypes.byref(b)))
     return b.value
+
+
+def zk_checkpoint_save(ctx):
+    """Checkpoint of the context (state spectra and IF-AB2 history) as host bytes."""
+    n = ctypes.c_size_t()
+    _check("zk_checkpoint_size", load().zk_checkpoint_size(ctx, ctypes.byref(n)))
+    buf = ctypes.create_string_buffer(n.value)
+    _check("zk_checkpoint_save", load().zk_checkpoint_save(ctx, buf, n.value))
+    return buf.raw
+
+
+def zk_checkpoint_load(ctx, data):
+    """Restore a checkpoint written by zk_checkpoint_save into a context of the same shape."""
+    buf = ctypes.create_string_buffer(bytes(data), len(data))
+    _check("zk_checkpoint_load", load().zk_checkpoint_load(ctx, buf, len(data)))
 
 
 def zk_launches_per_step(ctx):

@@ -47,3 +47,14 @@ def test_2d_backends_agree():
     np.testing.assert_allclose(fwd2(f, "dft"), fwd2(f, "fft"), atol=1e-10)
     F = fwd2(f, "fft")
     np.testing.assert_allclose(inv2(F, "dft").real, f, atol=1e-13)
+
+
+@pytest.mark.parametrize("shape", [(48, 96), (192, 128), (384, 384)])
+def test_fast_backend_matches_defining_sum(shape):
+    # the multi-threaded library backend against the literal sums, forward and inverse
+    rng = np.random.default_rng(shape[0])
+    f = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+    F = fwd2(f, "fft")
+    np.testing.assert_allclose(F, fwd2(f, "dft"), rtol=0, atol=1e-11 * np.max(np.abs(F)))
+    np.testing.assert_allclose(inv2(F, "fft"), inv2(F, "dft"), rtol=0, atol=1e-13 * np.max(np.abs(f)))
+    np.testing.assert_allclose(inv2(F, "fft"), f, rtol=0, atol=1e-13 * np.max(np.abs(f)))
