@@ -17,6 +17,12 @@ template <typename T> __device__ __forceinline__ T tanh_kh(T x);
 template <> __device__ __forceinline__ float tanh_kh<float>(float x) { return x > 9.5f ? 1.0f : tanhf(x); }
 template <> __device__ __forceinline__ double tanh_kh<double>(double x) { return x > 20.0 ? 1.0 : tanh(x); }
 
+// |k| from |k|^2 for the DNO symbols: FP32 contexts use the hardware reciprocal square
+// root (a few ulp, below the FP32 rounding of the products it scales); FP64 uses sqrt.
+template <typename T> __device__ __forceinline__ T d_kabs(T k2);
+template <> __device__ __forceinline__ float d_kabs<float>(float k2) { return k2 > 0.f ? k2 * rsqrtf(k2) : 0.f; }
+template <> __device__ __forceinline__ double d_kabs<double>(double k2) { return sqrt(k2); }
+
 template <typename T> __device__ __forceinline__ void d_sincos(T x, T* s, T* c);
 template <> __device__ __forceinline__ void d_sincos<float>(float x, float* s, float* c) { sincosf(x, s, c); }
 template <> __device__ __forceinline__ void d_sincos<double>(double x, double* s, double* c) { sincos(x, s, c); }
@@ -133,57 +139,76 @@ __global__ void __launch_bounds__(kRowMaxThreads) row2_kernel(const RowArgs<T> a
             return (s & 1) ? v.y : v.x;
         };
         TA* accrow = acc + (long long)zp * NPX;
-        for (int p = threadIdx.x; p < NPX; p += blockDim.x) {
+        // PB positions per iteration: their accumulator reads (global memory) are issued
+        // together, and the independent position updates interleave.
+        constexpr int PB = 4;
+        for (int p0 = threadIdx.x; p0 < NPX; p0 += PB * blockDim.x) {
+            const bool rd_acc = a.kind == 0 ? a.r >= 3 : a.M >= 3;
+            TA prev[PB];
+#pragma unroll
+            for (int j = 0; j < PB; ++j) {
+                const int p = p0 + j * blockDim.x;
+                prev[j] = (rd_acc && p < NPX) ? accrow[p] : (TA)0;
+            }
             if (a.kind == 0) {
                 const int r = a.r;
-                const TA eta = slot(a.s_eta, p);
-                TA W = 0, Phi = 0, ep = 1;
-                // unrolled over the largest order so that each 1/q is a constant (no division)
 #pragma unroll
-                for (int q = 1; q <= kMaxOrder; ++q) {
-                    if (q > r) break;
-                    const TA eq = ep * eta * (TA)(1.0 / q);
-                    const TA F = slot(a.s_F0 + (r - q), p);
-                    W += ep * F;
-                    Phi -= eq * F;
-                    ep = eq;
-                }
-                if (r >= 2) {
-                    TA coef = a.epsp[r - 1];
-                    if (r - 1 <= a.M - 3) {
-                        const TA ex = slot(a.s_etax, p), ez = slot(a.s_etaz, p);
-                        coef += (TA)a.epsp[r + 1] * (ex * ex + ez * ez);
+                for (int j = 0; j < PB; ++j) {
+                    const int p = p0 + j * blockDim.x;
+                    if (p >= NPX) break;
+                    const TA eta = slot(a.s_eta, p);
+                    TA W = 0, Phi = 0, ep = 1;
+                    // unrolled over the largest order so that each 1/q is a constant (no division)
+#pragma unroll
+                    for (int q = 1; q <= kMaxOrder; ++q) {
+                        if (q > r) break;
+                        const TA eq = ep * eta * (TA)(1.0 / q);
+                        const TA F = slot(a.s_F0 + (r - q), p);
+                        W += ep * F;
+                        Phi -= eq * F;
+                        ep = eq;
                     }
-                    const TA prev = (r == 2) ? (TA)0 : accrow[p];
-                    accrow[p] = prev + coef * W;
+                    if (r >= 2) {
+                        TA coef = a.epsp[r - 1];
+                        if (r - 1 <= a.M - 3) {
+                            const TA ex = slot(a.s_etax, p), ez = slot(a.s_etaz, p);
+                            coef += (TA)a.epsp[r + 1] * (ex * ex + ez * ez);
+                        }
+                        accrow[p] = prev[j] + coef * W;
+                    }
+                    lines[pidx(p)] = mk<T>((T)Phi, 0);
                 }
-                lines[pidx(p)] = mk<T>((T)Phi, 0);
             } else {
                 const int M = a.M;
                 const TA eps = a.eps;
-                const TA ex = slot(a.s_etax, p), ez = slot(a.s_etaz, p);
-                const TA px = slot(a.s_psix, p), pz = slot(a.s_psiz, p);
-                const TA g0 = slot(a.s_g0psi, p);
-                const TA g2 = ex * ex + ez * ez;
-                const TA d = ex * px + ez * pz;
-                const TA q2 = px * px + pz * pz;
-                TA Gnl = 0;
-                if (M >= 2) {
-                    const TA eta = slot(a.s_eta, p);
-                    TA W = 0, ep = 1;
 #pragma unroll
-                    for (int q = 1; q <= kMaxOrder; ++q) {
-                        if (q > M) break;
-                        W += ep * (TA)slot(a.s_F0 + (M - q), p);
-                        ep = ep * eta * (TA)(1.0 / q);
+                for (int j = 0; j < PB; ++j) {
+                    const int p = p0 + j * blockDim.x;
+                    if (p >= NPX) break;
+                    const TA ex = slot(a.s_etax, p), ez = slot(a.s_etaz, p);
+                    const TA px = slot(a.s_psix, p), pz = slot(a.s_psiz, p);
+                    const TA g0 = slot(a.s_g0psi, p);
+                    const TA g2 = ex * ex + ez * ez;
+                    const TA d = ex * px + ez * pz;
+                    const TA q2 = px * px + pz * pz;
+                    TA Gnl = 0;
+                    if (M >= 2) {
+                        const TA eta = slot(a.s_eta, p);
+                        TA W = 0, ep = 1;
+#pragma unroll
+                        for (int q = 1; q <= kMaxOrder; ++q) {
+                            if (q > M) break;
+                            W += ep * (TA)slot(a.s_F0 + (M - q), p);
+                            ep = ep * eta * (TA)(1.0 / q);
+                        }
+                        Gnl = (TA)a.epsp[M - 1] * W - eps * d;
+                        if (M >= 3) Gnl += prev[j] + (TA)a.epsp[2] * g2 * g0;
                     }
-                    Gnl = (TA)a.epsp[M - 1] * W - eps * d;
-                    if (M >= 3) Gnl += accrow[p] + (TA)a.epsp[2] * g2 * g0;
+                    const TA den = (TA)1 + (TA)a.epsp[2] * g2;
+                    const TA Wb = (g0 + Gnl + eps * d) / den;
+                    const TA Np = eps * ((TA)-0.5 * q2 + (TA)0.5 * den * Wb * Wb);
+                    lines[pidx(p)] = mk<T>((T)Gnl, (T)Np);
                 }
-                const TA den = (TA)1 + (TA)a.epsp[2] * g2;
-                const TA Wb = (g0 + Gnl + eps * d) / den;
-                const TA Np = eps * ((TA)-0.5 * q2 + (TA)0.5 * den * Wb * Wb);
-                lines[pidx(p)] = mk<T>((T)Gnl, (T)Np);
             }
         }
         __syncthreads();
@@ -364,7 +389,7 @@ col2_kernel(const ColArgs<T> a, const cx<T>* __restrict__ tw) {
                     const int e2 = aa >> 1;
                     for (int i = 0; i < e2; ++i) f *= k2;          // |k|^(2 floor(a/2))
                     if (aa & 1) {                                  // odd a: one more G0 = |k| tanh(|k| h)
-                        const T k = d_sqrt(k2);
+                        const T k = d_kabs(k2);
                         f *= k * tanh_kh(k * hh);
                     }
                     return cscale(s, f);
@@ -425,7 +450,7 @@ col2_kernel(const ColArgs<T> a, const cx<T>* __restrict__ tw) {
         const int ip = mz >= 0 ? mz : mz + NPZ;
         const T kxc = a.kx0 * (T)col;
         const T kz = a.kz0 * (T)mz;
-        const T k = d_sqrt(kxc * kxc + kz * kz);
+        const T k = d_kabs(kxc * kxc + kz * kz);
         T s = a.fscale;
         if (a.taper) s *= d_taper((kxc * kxc + kz * kz) * ikc2);
         const cx<T>* lc = sm + (size_t)cg * PER;
