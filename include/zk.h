@@ -380,7 +380,12 @@ zk_status zk_net_train_step(zk_net *n, const float *x, const float *target, int 
  * closure): mode 0 = the FP32 SIMT kernels above; mode 1 (the default) = 5th-generation
  * tensor cores (tcgen05 MMAs with FP32 accumulators in TMEM; the same FP16
  * rounding of weights and layer inputs, FP32 sums, so results agree with mode 0
- * to summation order). ZK_EINVAL for other modes. */
+ * to summation order). Every wait of a tensor-core block on its MMAs is bounded; a
+ * block whose wait runs out frees its TMEM and flags the call, which then returns
+ * ZK_ETIMEOUT. mode 2 = self-test of that path: the tensor-core kernels issue no MMA,
+ * so every wait runs out after a short limit and zk_net_predict returns ZK_ETIMEOUT
+ * with the network and the device still usable (its output is meaningless).
+ * ZK_EINVAL for other modes. */
 zk_status zk_net_set_inference(zk_net *n, int mode);
 /* y [2][nz][nx] = net(x [6][nz][nx]) for one sample with the current engine
  * (device arrays; nz, nx multiples of 16). Synchronises the stream;

@@ -291,7 +291,8 @@ struct zk_net {
     double* dpart = nullptr;  // loss partials [1024] + loss [1]
     const float* x = nullptr; // input of the last forward pass (caller memory)
     int B = 0, H = 0, W = 0;
-    int infer_mode = 1;       // inference on 0 = the FP32 SIMT kernels, 1 = tensor cores (default)
+    int infer_mode = 1;       // inference on 0 = the FP32 SIMT kernels, 1 = tensor cores (default),
+                              // 2 = tensor-core self-test with the MMAs withheld
     __half* wc = nullptr;     // canonical FP16 B operands of the tensor-core layers
     __half *a16 = nullptr, *b16 = nullptr;   // NHWC FP16 activations [H][W][32] (inference)
     int* err = nullptr;       // set by a tensor-core block whose MMA wait ran out
@@ -328,12 +329,13 @@ cudaError_t prepare(zk_net* n, cudaStream_t s) {
 
 template <int CINP, int CIN, bool IN_F32, int OUT>
 cudaError_t tc_layer(const void* x, const __half* wc, const float* bias, const float* w4, const float* b4, void* out,
-                     int H, int W, int* err, cudaStream_t s) {
+                     int H, int W, int* err, int withhold, cudaStream_t s) {
     constexpr int smem = zk_tc::conv_smem_bytes<CINP>();
     auto fn = zk_tc::conv3_tc_kernel<CINP, CIN, IN_F32, OUT>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    fn<<<dim3(W / zk_tc::kTileW, H / zk_tc::kTileH), zk_tc::kTilePx, smem, s>>>(x, wc, bias, w4, b4, out, H, W, err);
+    fn<<<dim3(W / zk_tc::kTileW, H / zk_tc::kTileH), zk_tc::kTilePx, smem, s>>>(x, wc, bias, w4, b4, out, H, W, err,
+                                                                                 withhold);
     return cudaGetLastError();
 }
 
@@ -342,13 +344,15 @@ cudaError_t tc_layer(const void* x, const __half* wc, const float* bias, const f
 cudaError_t tc_forward(zk_net* n, const float* x, int H, int W, cudaStream_t s) {
     cudaError_t e = prepare(n, s);
     const float* th = n->theta;
+    const int wh = n->infer_mode == 2 ? 1 : 0;
     if (e == cudaSuccess)
-        e = tc_layer<16, kCin, true, 0>(x, n->wc, th + boff(0), nullptr, nullptr, n->a16, H, W, n->err, s);
+        e = tc_layer<16, kCin, true, 0>(x, n->wc, th + boff(0), nullptr, nullptr, n->a16, H, W, n->err, wh, s);
     if (e == cudaSuccess)
-        e = tc_layer<32, kWidth, false, 0>(n->a16, n->wc + kTcOff2, th + boff(1), nullptr, nullptr, n->b16, H, W, n->err, s);
+        e = tc_layer<32, kWidth, false, 0>(n->a16, n->wc + kTcOff2, th + boff(1), nullptr, nullptr, n->b16, H, W, n->err,
+                                           wh, s);
     if (e == cudaSuccess)
         e = tc_layer<32, kWidth, false, 1>(n->b16, n->wc + kTcOff3, th + boff(2), n->w16 + woff(3), th + boff(3), n->y,
-                                           H, W, n->err, s);
+                                           H, W, n->err, wh, s);
     return e;
 }
 
@@ -422,7 +426,7 @@ zk_status zk_net_reserve(zk_net* n, size_t pixels) {
 cudaError_t zk_net_infer(zk_net* n, const float* x, const float** y, int B, int H, int W, cudaStream_t s) {
     if (!n || !y || !shape_ok(B, H, W) || (size_t)B * H * W > n->cap) return cudaErrorInvalidValue;
     *y = n->y;
-    if (n->infer_mode == 1 && B == 1) return tc_forward(n, x, H, W, s);
+    if (n->infer_mode >= 1 && B == 1) return tc_forward(n, x, H, W, s);
     return forward(n, x, B, H, W, s);
 }
 
@@ -470,7 +474,7 @@ zk_status zk_net_create(zk_net** out, int cin, int width, int cout) {
 }
 
 zk_status zk_net_set_inference(zk_net* n, int mode) {
-    if (!n || (mode != 0 && mode != 1)) return ZK_EINVAL;
+    if (!n || mode < 0 || mode > 2) return ZK_EINVAL;
     n->infer_mode = mode;
     return ZK_OK;
 }

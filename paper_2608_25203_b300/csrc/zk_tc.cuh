@@ -122,6 +122,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
 constexpr int kTileH = 8, kTileW = 16, kTilePx = kTileH * kTileW;
 constexpr int kCo = 32;
 constexpr uint32_t kWaitLimit = 1u << 22;   // mbarrier polls before the block gives up
+constexpr uint32_t kSelfTestWaitLimit = 64;  // polls per wait in the self-test of the give-up path
 
 // Taps per A chunk: the im2col tile is built and multiplied three taps at a
 // time, so a block needs a third of the A tile in shared memory and more
@@ -139,7 +140,7 @@ template <int CINP, int CIN, bool IN_F32, int OUT>
 __global__ void __launch_bounds__(128) conv3_tc_kernel(const void* __restrict__ xin, const __half* __restrict__ wcanon,
                                                        const float* __restrict__ bias, const float* __restrict__ w4,
                                                        const float* __restrict__ b4, void* __restrict__ out, int H,
-                                                       int W, int* __restrict__ err) {
+                                                       int W, int* __restrict__ err, int withhold) {
     constexpr int K = 9 * CINP, KC = kTaps * CINP;          // full K, K of one chunk
     constexpr int ABYTES = kTilePx * KC * 2, BBYTES = kCo * K * 2;
     static_assert(CINP % 16 == 0 && ABYTES % 1024 == 0, "operand tiles must stay 1 KB aligned");
@@ -156,11 +157,14 @@ __global__ void __launch_bounds__(128) conv3_tc_kernel(const void* __restrict__ 
         reinterpret_cast<uint4*>(Bs)[i] = __ldg(reinterpret_cast<const uint4*>(wcanon) + i);
     bool ok = true;
     uint32_t tbase = 0;
+    // withhold != 0 is the self-test of the give-up path: no MMA is issued and nothing is
+    // committed, so nothing is in flight and every wait below runs out after a short limit
+    const uint32_t limit = withhold ? kSelfTestWaitLimit : kWaitLimit;
 #pragma unroll 1
     for (int ch = 0; ch < 9 / kTaps; ++ch) {
         if (ch > 0) {
             // the previous chunk's MMAs read As: they must be done before it is refilled
-            ok = mbar_wait(&mbar, (ch - 1) & 1, kWaitLimit) && ok;
+            ok = mbar_wait(&mbar, (ch - 1) & 1, limit) && ok;
             fence_after_sync();
         }
         // im2col rows of this chunk's taps, all loads in flight together
@@ -191,7 +195,7 @@ __global__ void __launch_bounds__(128) conv3_tc_kernel(const void* __restrict__ 
         __syncthreads();
         fence_after_sync();
         tbase = tslot;
-        if (t == 0) {
+        if (t == 0 && !withhold) {
             const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
             constexpr uint32_t SBOA = (KC / 8) * 128, SBOB = (K / 8) * 128;
             constexpr uint32_t id = idesc_f16_f32(kTilePx, kCo);
@@ -204,8 +208,8 @@ __global__ void __launch_bounds__(128) conv3_tc_kernel(const void* __restrict__ 
     }
     {
         constexpr int last = 9 / kTaps - 1;
-        bool done = mbar_wait(&mbar, last & 1, kWaitLimit);
-        if (!done) done = mbar_wait(&mbar, last & 1, kWaitLimit);   // in-flight MMAs must finish before TMEM is freed
+        bool done = mbar_wait(&mbar, last & 1, limit);
+        if (!done) done = mbar_wait(&mbar, last & 1, limit);   // in-flight MMAs must finish before TMEM is freed
         ok = ok && done;
     }
     fence_after_sync();

@@ -57,4 +57,28 @@ def test_tensor_core_inference_is_deterministic(zk):
     torch.cuda.synchronize()
     assert torch.equal(a, b)
     with pytest.raises(zk.ZkError):
-        net.set_inference(2)
+        net.set_inference(3)
+
+
+def test_tensor_core_wait_gives_up_with_etimeout_and_recovers(zk):
+    """The bounded MMA waits of the tensor-core kernels run out (self-test mode 2: no MMA is
+    issued, so nothing is in flight and no wait can complete); every block frees its TMEM and
+    flags the call, zk_net_predict returns ZK_ETIMEOUT, and the same network then predicts
+    correctly on the tensor cores: the device and the context stay usable."""
+    import torch
+    rng = np.random.default_rng(5)
+    theta = cl.init_params(5).astype(np.float32)
+    x = rng.standard_normal((1, 6, 32, 32)).astype(np.float32)
+    net = zk.Net(theta)
+    xd = torch.from_numpy(x[0]).cuda().contiguous()
+    y = torch.empty((2, 32, 32), device="cuda")
+    net.set_inference(2)
+    for _ in range(2):
+        with pytest.raises(zk.ZkError) as ei:
+            net.predict(xd, y)
+        assert ei.value.status == zk.ZK_ETIMEOUT
+    net.set_inference(1)
+    net.predict(xd, y)
+    torch.cuda.synchronize()
+    yo, _ = cl.forward(theta.astype(np.float64), x.astype(np.float64))
+    assert rel(y.cpu().numpy(), yo[0]) < 1e-4
