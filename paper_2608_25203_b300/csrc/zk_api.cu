@@ -92,6 +92,7 @@ struct zk_ctx {
     int nfields = 0;
     long long fstride = 0;
     void *acc = nullptr;
+    void *sfc = nullptr;       // surface planes eta, dx eta, dz eta: [3][npz][npx] real per tile
     void *stage = nullptr;
     void *tank = nullptr;      // two (nx/2) x (nz/2) FP64-sized arrays for tank I/O
     double *partial = nullptr;
@@ -284,6 +285,9 @@ struct Pipe {
         a.occ = c->row_occ;
         a.acc64 = (sizeof(T) == 4 && c->series64) ? 1 : 0;
         a.pad3 = c->pad3 ? 1 : 0;
+        a.sfc = reinterpret_cast<T*>(c->sfc);
+        a.tsfc = 3 * c->tacc;
+        a.sfc_mode = 0;
         return a;
     }
 
@@ -344,24 +348,40 @@ struct Pipe {
             if ((e = launch_col<T>(c->npz, plan_of(c), c->col_ci, a, twz, s)) != cudaSuccess) return e;
             ++nl;
         }
+        // Surface planes (every order M >= 2): round 1 transforms eta, dx eta and dz eta once
+        // and writes them; the later rounds and the final round read them.
+        const bool sfc = c->sfc != nullptr && M >= 2;
+        const double Ps = (double)c->npz * c->npx * sizeof(T);                // one surface plane
         for (int r = 1; r <= M - 1; ++r) {
             RowArgs<T> ra = row_base(c);
             ra.kind = 0;
             ra.r = r;
             Slots sl{&ra};
-            ra.s_eta = sl.add(F.eta(), false);
-            if (r >= 2 && r - 1 <= M - 3) {
+            const bool g2 = r >= 2 && r - 1 <= M - 3;   // the round uses the slopes of eta
+            if (sfc && r == 1) {
+                ra.sfc_mode = 1;
+                ra.s_eta = sl.add(F.eta(), false);
                 ra.s_etax = sl.add(F.eta(), true);
                 ra.s_etaz = sl.add(F.dzeta(), false);
+            } else if (sfc) {
+                ra.sfc_mode = 2;
+            } else {
+                ra.s_eta = sl.add(F.eta(), false);
+                if (g2) {
+                    ra.s_etax = sl.add(F.eta(), true);
+                    ra.s_etaz = sl.add(F.dzeta(), false);
+                }
             }
             ra.s_F0 = sl.n;
             for (int j = 0; j < r; ++j) sl.add(F.z(j, r - j), false);
             sl.finish();
             ra.out0 = C(c->col) + (long long)F.phiout() * c->fstride;
             {
-                const bool g2 = r >= 2 && r - 1 <= M - 3;
-                const double rd = (1 + (g2 ? 1 : 0) + r) * U + (r >= 3 ? Pp : 0.0);
-                const double wr = U + (r >= 2 ? Pp : 0.0);
+                double rd, wr = U + (r >= 2 ? Pp : 0.0);
+                if (!sfc) rd = (1 + (g2 ? 1 : 0) + r) * U;
+                else if (r == 1) { rd = 2 * U + r * U; wr += 3 * Ps; }
+                else rd = r * U + (g2 ? 3 : 1) * Ps;
+                if (r >= 3) rd += Pp;
                 note(c, s, ZK_K_ROW_ROUND, rd + wr);
             }
             if ((e = launch_row<T>(c->npx, plan_of(c), ra, twx, c->npz, s)) != cudaSuccess) return e;
@@ -383,9 +403,13 @@ struct Pipe {
             ra.kind = 1;
             ra.r = M;
             Slots sl{&ra};
-            if (M >= 2) ra.s_eta = sl.add(F.eta(), false);
-            ra.s_etax = sl.add(F.eta(), true);
-            ra.s_etaz = sl.add(F.dzeta(), false);
+            if (sfc) {
+                ra.sfc_mode = 2;
+            } else {
+                if (M >= 2) ra.s_eta = sl.add(F.eta(), false);
+                ra.s_etax = sl.add(F.eta(), true);
+                ra.s_etaz = sl.add(F.dzeta(), false);
+            }
             ra.s_psix = sl.add(F.psi(), true);
             ra.s_psiz = sl.add(F.dzpsi(), false);
             ra.s_g0psi = sl.add(F.z(0, 1), false);
@@ -396,7 +420,8 @@ struct Pipe {
             sl.finish();
             ra.out0 = C(c->col) + (long long)F.gnl() * c->fstride;
             ra.out1 = C(c->col) + (long long)F.npsi() * c->fstride;
-            note(c, s, ZK_K_ROW_FINAL, (5 + (M >= 2 ? M : 0) + 2) * U + (M >= 3 ? Pp : 0.0));
+            note(c, s, ZK_K_ROW_FINAL,
+                 (sfc ? 3 * U + 3 * Ps : 5 * U) + ((M >= 2 ? M : 0) + 2) * U + (M >= 3 ? Pp : 0.0));
             if ((e = launch_row<T>(c->npx, plan_of(c), ra, twx, c->npz, s)) != cudaSuccess) return e;
             ++nl;
         }
@@ -957,6 +982,7 @@ zk_status ctx_create(zk_ctx** out, int nx, int nz, double Lx, double Lz, const d
     if (st == ZK_OK) st = dalloc(c, &c->col, (size_t)c->tcol * c->csz * nb);
     // 8 bytes per element in every precision, so FP32 contexts can switch on FP64 series sums
     if (st == ZK_OK) st = dalloc(c, &c->acc, (size_t)c->tacc * 8 * nb);
+    if (st == ZK_OK && M >= 2) st = dalloc(c, &c->sfc, (size_t)3 * c->tacc * rsz * nb);
     if (st == ZK_OK) st = dalloc(c, &c->stage, (size_t)2 * nx * nz * kIoElem);
     if (st == ZK_OK) st = dalloc(c, &c->tank, (size_t)2 * (nx / 2) * (nz / 2) * 8);
     c->npartial = c->hx * nb;              // at most one column-kernel block per column
@@ -994,6 +1020,7 @@ void tile_view(const zk_ctx* g, int t, zk_ctx* v) {
     v->h_eta = off(g->h_eta, oc); v->h_psi = off(g->h_psi, oc);
     v->col = off(g->col, (size_t)t * g->tcol * g->csz);
     v->acc = off(g->acc, (size_t)t * g->tacc * ((g->prec == ZK_F32 && !g->series64) ? 4 : 8));
+    v->sfc = off(g->sfc, (size_t)t * 3 * g->tacc * (g->prec == ZK_F32 ? 4 : 8));
     v->series64 = g->series64;
     v->pad3 = g->pad3;
     v->nfields = g->nfields;

@@ -157,10 +157,14 @@ template <bool INV, typename T> struct SmallDFT<16, INV, T> {
 __host__ __device__ constexpr int pidx(int i) { return i + (i >> 4); }
 __host__ __device__ constexpr int line_stride(int N) { return N + (N >> 4) + 1; }
 
+// A negative barrier id stands for the whole block (a block of exactly one line group). Kernels
+// that pass a constant -1 then use barrier 0 alone: the named barriers a block reserves (16 when
+// the id is a run-time value) cap how many blocks an SM holds.
 template <int TL>
 __device__ __forceinline__ void group_sync(int bar) {
     if constexpr (TL > 32) {
-        asm volatile("bar.sync %0, %1;" ::"r"(bar), "n"(TL) : "memory");
+        if (bar < 0) __syncthreads();
+        else asm volatile("bar.sync %0, %1;" ::"r"(bar), "n"(TL) : "memory");
     } else {
         __syncwarp();
     }

@@ -222,7 +222,8 @@ __device__ __forceinline__ void dit_last_blk(const cx<T>* buf, const cx<T>* __re
 // transform, where one line is shared by the threads of several line groups.
 template <int TLB>
 __device__ __forceinline__ void wide_sync(int bar) {
-    asm volatile("bar.sync %0, %1;" ::"r"(bar), "n"(TLB) : "memory");
+    if (bar < 0) __syncthreads();   // the group is the whole block (see group_sync)
+    else asm volatile("bar.sync %0, %1;" ::"r"(bar), "n"(TLB) : "memory");
 }
 
 template <int N, int B, int R, int TLB, bool INV, typename T, int OFF>

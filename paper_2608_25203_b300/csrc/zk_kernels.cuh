@@ -6,15 +6,18 @@
 // column is not stored, the z Nyquist row is held at zero). A "column-space"
 // field is [npz][nx/2] complex: z already transformed to the 3/2-padded
 // physical grid (npz = 3 nz / 2), x still spectral. Padded physical fields
-// ([npz][npx]) never reach global memory except the series accumulator.
+// ([npz][npx]) reach global memory only as the series accumulator and the
+// three surface planes eta, dx eta, dz eta (written by round 1, read by the
+// later rounds instead of transforming the same three fields again).
 //
 // The launches of one right-hand side (kernels in zk_kernels2.cuh):
 //  col2_kernel COL_FROM_STATE: per kx column, read the stage state
 //      eta_hat, psi_hat and write column-space eta, dz eta, psi, dz psi and
 //      dz^a psi for a = 1..M (zero padding, inverse column FFT).
 //  row2_kernel round r = 1..M-1: per padded row, inverse row FFTs of
-//      eta, [dx eta, dz eta], F_j = dz^{r-j} Phi(j) (j < r) into physical
-//      space; pointwise Phi(r) = -sum eta^{r-j}/(r-j)! F_j and
+//      F_j = dz^{r-j} Phi(j) (j < r) into physical space (round 1 also
+//      transforms eta, dx eta, dz eta and writes the surface planes; later
+//      rounds read them); pointwise Phi(r) = -sum eta^{r-j}/(r-j)! F_j and
 //      W(r-1) = sum eta^{r-1-j}/(r-1-j)! F_j; W(r-1) folded into the series
 //      accumulator with its eps and |grad eta|^2 weights; forward row FFT of
 //      Phi(r) into column space.
@@ -80,6 +83,13 @@ struct RowArgs {
     int occ;                 // host side: resident blocks per SM to use (0 = all)
     int acc64;               // host side: series sums in FP64 (FP32 contexts; acc holds doubles)
     int pad3;                // host side: 3N padding (kernels with DIV = 6)
+    // Surface planes: eta, d eta/dx, d eta/dz on the padded grid, [3][npz][npx] (positions in
+    // the row plan's digit-reversed order). sfc_mode 0: not used (the round transforms them
+    // from their slots); 1: the round transforms them and writes the planes; 2: the round
+    // reads them from the planes and has no slots for them. tsfc: one tile's element offset.
+    T* sfc;
+    long long tsfc;
+    int sfc_mode;
 };
 
 // ---------------------------------------------------------------------------

@@ -56,7 +56,9 @@ constexpr int kRowMaxThreads = ZK_ROW_MAX_THREADS;
 
 
 // DIV = NPX / (nx / 2): 3 for the 3/2 rule, 6 for the 3N padding.
-template <typename T, int NPX, int V = 0, typename TA = T, int DIV = 3>
+// ONEG: the block is a single line group (rounds with one line): every barrier is barrier 0,
+// so the block reserves one hardware barrier instead of 16 and more blocks fit on an SM.
+template <typename T, int NPX, int V = 0, typename TA = T, int DIV = 3, bool ONEG = false>
 __global__ void __launch_bounds__(kRowMaxThreads) row2_kernel(const RowArgs<T> a, const cx<T>* __restrict__ tw) {
     using P = IPlan<NPX, V>;
     constexpr int TL = P::TL;
@@ -64,8 +66,8 @@ __global__ void __launch_bounds__(kRowMaxThreads) row2_kernel(const RowArgs<T> a
     constexpr int LS = line_stride(NPX);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<T>* lines = reinterpret_cast<cx<T>*>(smem_raw);
-    const int g = threadIdx.x / TL, lt = threadIdx.x % TL;
-    const int bar = 1 + (g & 7);
+    const int g = ONEG ? 0 : threadIdx.x / TL, lt = ONEG ? threadIdx.x : threadIdx.x % TL;
+    const int bar = ONEG ? -1 : 1 + (g & 7);
     const int ngroups = blockDim.x / TL;
     // wide groups (TL >= 32) take lines in waves; narrow groups share warps and
     // each runs exactly one line (idle ones on zeros) so warp barriers match
@@ -79,26 +81,39 @@ __global__ void __launch_bounds__(kRowMaxThreads) row2_kernel(const RowArgs<T> a
 
     // the series accumulator row is read by rounds r >= 3 and by the final round when M >= 3
     const bool reads_acc = a.kind == 0 ? a.r >= 3 : a.M >= 3;
+    // the slopes of eta enter round r when r - 1 <= M - 3, and always the final round
+    const bool slopes = a.kind == 0 ? (a.r >= 2 && a.r - 1 <= a.M - 3) : true;
+    const bool eta_in = a.kind == 0 || a.M >= 2;
+    // surface planes of this tile: eta, dx eta, dz eta, PL elements apart
+    const long long PL = (long long)a.npz * NPX;
+    T* sfc = a.sfc_mode ? a.sfc + (long long)blockIdx.y * a.tsfc : nullptr;
+    const int npl = a.sfc_mode == 2 ? (slopes ? 3 : (eta_in ? 1 : 0)) : 0;   // planes read
     for (int zp = blockIdx.x; zp < a.npz; zp += gridDim.x) {
-        // Ask L2 for this block's next row now: its input lines (HX contiguous values per field)
-        // and accumulator row then arrive while the current row is transformed. Sizes and
-        // addresses are multiples of 16 bytes (HX, the field stride and NPX are even).
-        // Grids below 1024 points per axis keep their fields in L2 and would only pay the
-        // instructions.
+        // Ask L2 for this block's next row now: its input lines (HX contiguous values per field),
+        // accumulator row and surface-plane rows then arrive while the current row is
+        // transformed. Sizes and addresses are multiples of 16 bytes (HX, the field stride and
+        // NPX are even; NPX is a multiple of 4). Grids below 1024 points per axis keep their
+        // fields in L2 and would only pay the instructions.
         const int zn = zp + gridDim.x;
-        if (NPX >= 1536 && zn < a.npz && threadIdx.x <= 2 * a.nlines) {
+        if (NPX >= 1536 && zn < a.npz && threadIdx.x <= 2 * a.nlines + npl) {
             const void* src = nullptr;
             unsigned bytes = 0;
-            if (threadIdx.x < 2 * a.nlines) {
-                const int l = threadIdx.x >> 1;
-                const int f = (threadIdx.x & 1) ? a.fb[l] : a.fa[l];
+            const int t = threadIdx.x;
+            if (t < 2 * a.nlines) {
+                const int l = t >> 1;
+                const int f = (t & 1) ? a.fb[l] : a.fa[l];
                 if (f >= 0) {
                     src = colbase + (long long)f * a.fstride + (long long)zn * HX;
                     bytes = (unsigned)(HX * sizeof(cx<T>));
                 }
-            } else if (reads_acc) {
-                src = acc + (long long)zn * NPX;
-                bytes = (unsigned)(NPX * sizeof(TA));
+            } else if (t == 2 * a.nlines) {
+                if (reads_acc) {
+                    src = acc + (long long)zn * NPX;
+                    bytes = (unsigned)(NPX * sizeof(TA));
+                }
+            } else {
+                src = sfc + (long long)(t - 2 * a.nlines - 1) * PL + (long long)zn * NPX;
+                bytes = (unsigned)(NPX * sizeof(T));
             }
             if (src) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
         }
@@ -139,16 +154,35 @@ __global__ void __launch_bounds__(kRowMaxThreads) row2_kernel(const RowArgs<T> a
             return (s & 1) ? v.y : v.x;
         };
         TA* accrow = acc + (long long)zp * NPX;
-        // PB positions per iteration: their accumulator reads (global memory) are issued
-        // together, and the independent position updates interleave.
+        T* srow = sfc ? sfc + (long long)zp * NPX : nullptr;
+        // eta and its slopes at position p: from the surface planes (mode 2, preloaded into
+        // se[] below) or from their slots in the transformed lines
+        const bool rd_sfc = a.sfc_mode == 2;
+        // PB positions per iteration: their accumulator and surface-plane reads (global
+        // memory) are issued together, and the independent position updates interleave.
         constexpr int PB = 4;
         for (int p0 = threadIdx.x; p0 < NPX; p0 += PB * blockDim.x) {
             const bool rd_acc = a.kind == 0 ? a.r >= 3 : a.M >= 3;
             TA prev[PB];
+            T se[3][PB];
 #pragma unroll
             for (int j = 0; j < PB; ++j) {
                 const int p = p0 + j * blockDim.x;
-                prev[j] = (rd_acc && p < NPX) ? accrow[p] : (TA)0;
+                const bool in = p < NPX;
+                prev[j] = (rd_acc && in) ? accrow[p] : (TA)0;
+                se[0][j] = (rd_sfc && eta_in && in) ? __ldg(srow + p) : (T)0;
+                se[1][j] = (rd_sfc && slopes && in) ? __ldg(srow + PL + p) : (T)0;
+                se[2][j] = (rd_sfc && slopes && in) ? __ldg(srow + 2 * PL + p) : (T)0;
+            }
+            if (a.sfc_mode == 1) {
+#pragma unroll
+                for (int j = 0; j < PB; ++j) {
+                    const int p = p0 + j * blockDim.x;
+                    if (p >= NPX) break;
+                    srow[p] = (T)slot(a.s_eta, p);
+                    srow[PL + p] = (T)slot(a.s_etax, p);
+                    srow[2 * PL + p] = (T)slot(a.s_etaz, p);
+                }
             }
             if (a.kind == 0) {
                 const int r = a.r;
@@ -156,7 +190,7 @@ __global__ void __launch_bounds__(kRowMaxThreads) row2_kernel(const RowArgs<T> a
                 for (int j = 0; j < PB; ++j) {
                     const int p = p0 + j * blockDim.x;
                     if (p >= NPX) break;
-                    const TA eta = slot(a.s_eta, p);
+                    const TA eta = rd_sfc ? (TA)se[0][j] : slot(a.s_eta, p);
                     TA W = 0, Phi = 0, ep = 1;
                     // unrolled over the largest order so that each 1/q is a constant (no division)
 #pragma unroll
@@ -171,7 +205,8 @@ __global__ void __launch_bounds__(kRowMaxThreads) row2_kernel(const RowArgs<T> a
                     if (r >= 2) {
                         TA coef = a.epsp[r - 1];
                         if (r - 1 <= a.M - 3) {
-                            const TA ex = slot(a.s_etax, p), ez = slot(a.s_etaz, p);
+                            const TA ex = rd_sfc ? (TA)se[1][j] : slot(a.s_etax, p);
+                            const TA ez = rd_sfc ? (TA)se[2][j] : slot(a.s_etaz, p);
                             coef += (TA)a.epsp[r + 1] * (ex * ex + ez * ez);
                         }
                         accrow[p] = prev[j] + coef * W;
@@ -185,7 +220,8 @@ __global__ void __launch_bounds__(kRowMaxThreads) row2_kernel(const RowArgs<T> a
                 for (int j = 0; j < PB; ++j) {
                     const int p = p0 + j * blockDim.x;
                     if (p >= NPX) break;
-                    const TA ex = slot(a.s_etax, p), ez = slot(a.s_etaz, p);
+                    const TA ex = rd_sfc ? (TA)se[1][j] : slot(a.s_etax, p);
+                    const TA ez = rd_sfc ? (TA)se[2][j] : slot(a.s_etaz, p);
                     const TA px = slot(a.s_psix, p), pz = slot(a.s_psiz, p);
                     const TA g0 = slot(a.s_g0psi, p);
                     const TA g2 = ex * ex + ez * ez;
@@ -193,7 +229,7 @@ __global__ void __launch_bounds__(kRowMaxThreads) row2_kernel(const RowArgs<T> a
                     const TA q2 = px * px + pz * pz;
                     TA Gnl = 0;
                     if (M >= 2) {
-                        const TA eta = slot(a.s_eta, p);
+                        const TA eta = rd_sfc ? (TA)se[0][j] : slot(a.s_eta, p);
                         TA W = 0, ep = 1;
 #pragma unroll
                         for (int q = 1; q <= kMaxOrder; ++q) {
@@ -218,7 +254,9 @@ __global__ void __launch_bounds__(kRowMaxThreads) row2_kernel(const RowArgs<T> a
         {
             cx<T>* o0 = out0 + (long long)zp * HX;
             auto fwd0 = [&](auto st) {
-                if constexpr (TL >= 32) {
+                if constexpr (ONEG) {
+                    P::template dit_wide<TL, false, T>(lines, tw, threadIdx.x, -1, st);
+                } else if constexpr (TL >= 32) {
                     constexpr int kBarC = 15;
                     const int ng = blockDim.x / TL;
                     if (ng == 3) {
@@ -386,8 +424,11 @@ col2_kernel(const ColArgs<T> a, const cx<T>* __restrict__ tw) {
                     if (sym == SYM_DZ) return cscale(mk<T>(-kz * s.y, kz * s.x), isc);
                     const T k2 = kx * kx + kz * kz;
                     T f = isc;
+                    // |k|^(2 floor(a/2)), a <= kMaxOrder: predicated products, no per-element loop
                     const int e2 = aa >> 1;
-                    for (int i = 0; i < e2; ++i) f *= k2;          // |k|^(2 floor(a/2))
+#pragma unroll
+                    for (int i = 0; i < kMaxOrder / 2; ++i)
+                        if (i < e2) f *= k2;
                     if (aa & 1) {                                  // odd a: one more G0 = |k| tanh(|k| h)
                         const T k = d_kabs(k2);
                         f *= k * tanh_kh(k * hh);

@@ -20,7 +20,10 @@ cudaError_t launch_row_t(const RowArgs<T>& a, const cx<T>* tw, int npz, cudaStre
     const int threads = groups * TL;
     const size_t smem = (size_t)nl * line_stride(NPX) * sizeof(cx<T>);
     if (threads > 1024 || smem > (size_t)smem_optin()) return cudaErrorInvalidConfiguration;
-    const void* fn = (const void*)row2_kernel<T, NPX, V, TA, DIV>;
+    // a block of one wide line group synchronises on barrier 0 alone (more blocks per SM)
+    const bool oneg = TL >= 32 && groups == 1;
+    const void* fn = oneg ? (const void*)row2_kernel<T, NPX, V, TA, DIV, true>
+                          : (const void*)row2_kernel<T, NPX, V, TA, DIV, false>;
     cudaError_t e = ensure_smem(fn, smem);
     if (e != cudaSuccess) return e;
     RowArgs<T> b = a;
@@ -32,7 +35,8 @@ cudaError_t launch_row_t(const RowArgs<T>& a, const cx<T>* tw, int npz, cudaStre
     if (a.occ > 0) per_sm = std::min(per_sm, a.occ);
     const int nb = std::max(1, a.nb);
     const int gx = std::max(1, std::min(npz, (per_sm * sms + nb - 1) / nb));
-    row2_kernel<T, NPX, V, TA, DIV><<<dim3(gx, nb), threads, smem, s>>>(b, tw);
+    if (oneg) row2_kernel<T, NPX, V, TA, DIV, true><<<dim3(gx, nb), threads, smem, s>>>(b, tw);
+    else row2_kernel<T, NPX, V, TA, DIV, false><<<dim3(gx, nb), threads, smem, s>>>(b, tw);
     return cudaGetLastError();
 }
 
