@@ -42,6 +42,10 @@ struct zk_ctx {
     size_t csz = 0;  // bytes per complex element
     void *tw_x = nullptr, *tw_z = nullptr, *tw_px = nullptr, *tw_pz = nullptr;
     void* tw_pv[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};   // padded plan tables [variant][x, z]
+    // half-length plan tables of the padded rows [variant] (nullptr where the plan of npx has
+    // no half-length form) and w_npx^k, k < npx/2: the real forward row transform at half length
+    void* tw_hv[2] = {nullptr, nullptr};
+    void* tw_rx = nullptr;
     // tiles sharing this grid and order (a batch group; 1 for a plain context):
     // buffers are [tile][...] with these element strides, depth per tile
     int nb = 1;
@@ -288,6 +292,11 @@ struct Pipe {
         a.sfc = reinterpret_cast<T*>(c->sfc);
         a.tsfc = 3 * c->tacc;
         a.sfc_mode = 0;
+        // half-length real forward transform: plans 0 / 1 only (the split-precision plans keep
+        // the full-length transform); the kernel falls back where its block shape does not fit
+        const int pv = plan_of(c);
+        a.twh = (pv == 0 || pv == 1) && c->tw_rx ? reinterpret_cast<const cx<T>*>(c->tw_hv[pv]) : nullptr;
+        a.twr = a.twh ? reinterpret_cast<const cx<T>*>(c->tw_rx) : nullptr;
         return a;
     }
 
@@ -814,6 +823,21 @@ zk_status alloc_twiddles(zk_ctx* c) {
     }
     c->tw_px = c->tw_pv[0][0];
     c->tw_pz = c->tw_pv[0][1];
+    bool any_half = false;
+    for (int v = 0; v < 2 && st == ZK_OK; ++v) {
+        if (!half_plan_ok_host(c->npx, v)) continue;
+        make_plan_twiddles<T>(c->npx / 2, v, h);
+        st = upload<T>(c, h, &c->tw_hv[v]);
+        any_half = true;
+    }
+    if (st == ZK_OK && any_half) {
+        h.resize(c->npx / 2);
+        for (int k = 0; k < c->npx / 2; ++k) {
+            const double ang = -2.0 * M_PI * (double)k / (double)c->npx;
+            h[k] = mk<T>((T)std::cos(ang), (T)std::sin(ang));
+        }
+        st = upload<T>(c, h, &c->tw_rx);
+    }
     return st;
 }
 
@@ -1011,6 +1035,9 @@ void tile_view(const zk_ctx* g, int t, zk_ctx* v) {
     v->has_state = true;
     v->csz = g->csz;
     v->tw_x = g->tw_x; v->tw_z = g->tw_z; v->tw_px = g->tw_px; v->tw_pz = g->tw_pz;
+    v->tw_pv[0][0] = g->tw_pv[0][0]; v->tw_pv[0][1] = g->tw_pv[0][1];
+    v->tw_pv[1][0] = g->tw_pv[1][0]; v->tw_pv[1][1] = g->tw_pv[1][1];
+    v->tw_hv[0] = g->tw_hv[0]; v->tw_hv[1] = g->tw_hv[1]; v->tw_rx = g->tw_rx;
     const size_t oc = (size_t)t * g->tst * g->csz;
     auto off = [&](void* p, size_t o) { return p ? (void*)((char*)p + o) : nullptr; };
     v->y_eta = off(g->y_eta, oc); v->y_psi = off(g->y_psi, oc);

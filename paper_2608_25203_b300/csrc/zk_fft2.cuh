@@ -378,6 +378,29 @@ inline PlanDesc plan_desc_of(int n, int v = 0) {
     default: return PlanDesc{0, 0, {1, 1, 1, 1}};
     }
 }
+// Half-length plan of a real line: when the plan of N starts with an even radix R1 and the plan
+// of N/2 is (R1/2, same later radices), the DIF output slot s = m1 (N/R1) + r (first digit m1)
+// holds the same physical position as slot (m1/2) (N/R1) + r of the N/2 plan, times two, plus
+// (m1 mod 2). A real line x of N points can then be packed as z[n] = x[2n] + i x[2n+1] with no
+// reordering and transformed at half length (the forward real-input transform of the row
+// rounds). Host and device read the same plan descriptions.
+inline __host__ __device__ constexpr bool half_plan_match(const PlanDesc& d, const PlanDesc& h) {
+    if (d.n < 48 || d.n % 2 != 0 || h.n * 2 != d.n || d.nstage != h.nstage) return false;
+    if (d.radix[0] % 2 != 0 || h.radix[0] * 2 != d.radix[0]) return false;
+    for (int i = 1; i < d.nstage; ++i)
+        if (d.radix[i] != h.radix[i]) return false;
+    return true;
+}
+template <int N, int V> __host__ __device__ constexpr bool half_plan_ok() {
+    if constexpr (N < 48 || N % 2 != 0 || (V != 0 && V != 1)) return false;
+    else return half_plan_match(plan_desc<N, V>(), plan_desc<N / 2, V>());
+}
+inline bool half_plan_ok_host(int n, int v) {
+    if (n < 48 || n % 2 != 0 || (v != 0 && v != 1)) return false;
+    const PlanDesc d = plan_desc_of(n, v), h = plan_desc_of(n / 2, v);
+    return d.n == n && h.n == n / 2 && half_plan_match(d, h);
+}
+
 // Number of table entries, and entry e as (numerator, B) of the angle -2 pi num / B.
 inline int plan_table_size(const PlanDesc& d) {
     int n = 0, B = d.n;

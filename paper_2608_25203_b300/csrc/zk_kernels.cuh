@@ -90,6 +90,10 @@ struct RowArgs {
     T* sfc;
     long long tsfc;
     int sfc_mode;
+    // Half-length forward transform of the real Phi(r) (intermediate rounds): the table of the
+    // N/2 plan and w_N^k = exp(-2 pi i k / N) for k < N/2; nullptr = full-length transform.
+    const cx<T>* twh;
+    const cx<T>* twr;
 };
 
 // ---------------------------------------------------------------------------

@@ -48,12 +48,32 @@ template <> __device__ __forceinline__ double d_taper<double>(double u2) {
 // FP32 contexts with FP64 series accumulation (the accumulator buffer then
 // holds doubles).
 // Largest row-kernel block: it bounds the registers a thread may use (the
-// line groups of a wider round take their lines in waves).
+// line groups of a wider round take their lines in waves). 512 threads leave
+// 128 registers: the transforms then run without register pressure, at 16
+// warps per SM (measured faster than 24-32 warps at 64 registers).
 #ifndef ZK_ROW_MAX_THREADS
-#define ZK_ROW_MAX_THREADS 1024
+#define ZK_ROW_MAX_THREADS 512
 #endif
 constexpr int kRowMaxThreads = ZK_ROW_MAX_THREADS;
 
+
+// Read-once global loads: an L2 evict-first cache policy (created once per thread) keeps them
+// from displacing data that is still to be used.
+__device__ __forceinline__ unsigned long long l2_evict_first_policy() {
+    unsigned long long pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ float ldg_evict_first(const float* p, unsigned long long pol) {
+    float v;
+    asm volatile("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ double ldg_evict_first(const double* p, unsigned long long pol) {
+    double v;
+    asm volatile("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
+    return v;
+}
 
 // DIV = NPX / (nx / 2): 3 for the 3/2 rule, 6 for the 3N padding.
 // ONEG: the block is a single line group (rounds with one line): every barrier is barrier 0,
@@ -74,6 +94,11 @@ __global__ void __launch_bounds__(kRowMaxThreads) row2_kernel(const RowArgs<T> a
     const int nloop = TL < 32 ? ngroups : a.nlines;
     const T kx0 = a.kx0;
     constexpr int SUB1 = NPX / P::R1;
+    // Phi(r) (real) forward-transformed at half length: Phase B packs x[2n] + i x[2n+1] in
+    // place (a position's new slot belongs to the same thread and to a position it has already
+    // read, when the block width divides SUB1), Phase C runs the N/2 plan and splits the result.
+    constexpr bool HALF_OK = TL >= 32 && half_plan_ok<NPX, V>();
+    const bool half = HALF_OK && a.kind == 0 && a.twh != nullptr && (SUB1 % blockDim.x) == 0;
     const cx<T>* colbase = a.colbase + (long long)blockIdx.y * a.tcol;
     TA* acc = reinterpret_cast<TA*>(a.acc) + (long long)blockIdx.y * a.tacc;
     cx<T>* out0 = a.out0 + (long long)blockIdx.y * a.tcol;
@@ -88,35 +113,9 @@ __global__ void __launch_bounds__(kRowMaxThreads) row2_kernel(const RowArgs<T> a
     const long long PL = (long long)a.npz * NPX;
     T* sfc = a.sfc_mode ? a.sfc + (long long)blockIdx.y * a.tsfc : nullptr;
     const int npl = a.sfc_mode == 2 ? (slopes ? 3 : (eta_in ? 1 : 0)) : 0;   // planes read
+    // the planes are read once per round: their L2 lines go first, before the rows in flight
+    const unsigned long long pol = l2_evict_first_policy();
     for (int zp = blockIdx.x; zp < a.npz; zp += gridDim.x) {
-        // Ask L2 for this block's next row now: its input lines (HX contiguous values per field),
-        // accumulator row and surface-plane rows then arrive while the current row is
-        // transformed. Sizes and addresses are multiples of 16 bytes (HX, the field stride and
-        // NPX are even; NPX is a multiple of 4). Grids below 1024 points per axis keep their
-        // fields in L2 and would only pay the instructions.
-        const int zn = zp + gridDim.x;
-        if (NPX >= 1536 && zn < a.npz && threadIdx.x <= 2 * a.nlines + npl) {
-            const void* src = nullptr;
-            unsigned bytes = 0;
-            const int t = threadIdx.x;
-            if (t < 2 * a.nlines) {
-                const int l = t >> 1;
-                const int f = (t & 1) ? a.fb[l] : a.fa[l];
-                if (f >= 0) {
-                    src = colbase + (long long)f * a.fstride + (long long)zn * HX;
-                    bytes = (unsigned)(HX * sizeof(cx<T>));
-                }
-            } else if (t == 2 * a.nlines) {
-                if (reads_acc) {
-                    src = acc + (long long)zn * NPX;
-                    bytes = (unsigned)(NPX * sizeof(TA));
-                }
-            } else {
-                src = sfc + (long long)(t - 2 * a.nlines - 1) * PL + (long long)zn * NPX;
-                bytes = (unsigned)(NPX * sizeof(T));
-            }
-            if (src) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
-        }
         // Phase A: Hermitian packing of two real fields fused into the first DIF stage.
         for (int l = g; l < nloop; l += ngroups) {
             cx<T>* lb = lines + (size_t)l * LS;
@@ -148,6 +147,36 @@ __global__ void __launch_bounds__(kRowMaxThreads) row2_kernel(const RowArgs<T> a
         }
         __syncthreads();
 
+        // Ask L2 for this block's next row once this row's inputs are in: its input lines (HX
+        // contiguous values per field), accumulator row and surface-plane rows then arrive while
+        // the current row's pointwise phase and forward transform run. Issued a whole row
+        // earlier, the prefetched rows of all resident blocks outgrew L2 and were partly evicted
+        // before use. Sizes and addresses are multiples of 16 bytes (HX, the field stride and
+        // NPX are even; NPX is a multiple of 4). Grids below 1024 points per axis keep their
+        // fields in L2 and would only pay the instructions.
+        const int zn = zp + gridDim.x;
+        if (NPX >= 1536 && zn < a.npz && threadIdx.x <= 2 * a.nlines + npl) {
+            const void* src = nullptr;
+            unsigned bytes = 0;
+            const int t = threadIdx.x;
+            if (t < 2 * a.nlines) {
+                const int l = t >> 1;
+                const int f = (t & 1) ? a.fb[l] : a.fa[l];
+                if (f >= 0) {
+                    src = colbase + (long long)f * a.fstride + (long long)zn * HX;
+                    bytes = (unsigned)(HX * sizeof(cx<T>));
+                }
+            } else if (t == 2 * a.nlines) {
+                if (reads_acc) {
+                    src = acc + (long long)zn * NPX;
+                    bytes = (unsigned)(NPX * sizeof(TA));
+                }
+            } else {
+                src = sfc + (long long)(t - 2 * a.nlines - 1) * PL + (long long)zn * NPX;
+                bytes = (unsigned)(NPX * sizeof(T));
+            }
+            if (src) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+        }
         // Phase B: pointwise HOS terms (positions in digit-reversed order).
         auto slot = [&](int s, int p) -> T {
             const cx<T> v = lines[(s >> 1) * LS + pidx(p)];
@@ -170,9 +199,9 @@ __global__ void __launch_bounds__(kRowMaxThreads) row2_kernel(const RowArgs<T> a
                 const int p = p0 + j * blockDim.x;
                 const bool in = p < NPX;
                 prev[j] = (rd_acc && in) ? accrow[p] : (TA)0;
-                se[0][j] = (rd_sfc && eta_in && in) ? __ldg(srow + p) : (T)0;
-                se[1][j] = (rd_sfc && slopes && in) ? __ldg(srow + PL + p) : (T)0;
-                se[2][j] = (rd_sfc && slopes && in) ? __ldg(srow + 2 * PL + p) : (T)0;
+                se[0][j] = (rd_sfc && eta_in && in) ? ldg_evict_first(srow + p, pol) : (T)0;
+                se[1][j] = (rd_sfc && slopes && in) ? ldg_evict_first(srow + PL + p, pol) : (T)0;
+                se[2][j] = (rd_sfc && slopes && in) ? ldg_evict_first(srow + 2 * PL + p, pol) : (T)0;
             }
             if (a.sfc_mode == 1) {
 #pragma unroll
@@ -211,7 +240,16 @@ __global__ void __launch_bounds__(kRowMaxThreads) row2_kernel(const RowArgs<T> a
                         }
                         accrow[p] = prev[j] + coef * W;
                     }
-                    lines[pidx(p)] = mk<T>((T)Phi, 0);
+                    if (HALF_OK && half) {
+                        // slot m1 SUB1 + q of the N plan -> component (m1 mod 2) of slot
+                        // (m1 / 2) SUB1 + q of the N/2 plan
+                        const int m1 = p / SUB1;
+                        cx<T>& dst = lines[pidx(p - (m1 - (m1 >> 1)) * SUB1)];
+                        if (m1 & 1) dst.y = (T)Phi;
+                        else dst.x = (T)Phi;
+                    } else {
+                        lines[pidx(p)] = mk<T>((T)Phi, 0);
+                    }
                 }
             } else {
                 const int M = a.M;
@@ -272,11 +310,36 @@ __global__ void __launch_bounds__(kRowMaxThreads) row2_kernel(const RowArgs<T> a
                     P::template dit_blk<false, T>(lines, tw, threadIdx.x, blockDim.x, st);
                 }
             };
-            if (a.kind == 0) {
+            if constexpr (HALF_OK) {
+                if (half) {
+                    // Z = DFT_{N/2}(x[2n] + i x[2n+1]); X[k] = E[k] + w_N^k O[k] with
+                    // E = (Z[k] + conj Z[N/2-k]) / 2 and O = (Z[k] - conj Z[N/2-k]) / 2i
+                    using PH = IPlan<NPX / 2, V>;
+                    constexpr int NH = NPX / 2;
+                    auto sth = [&](int k, cx<T> v) { lines[pidx(k)] = v; };
+                    if constexpr (ONEG) {
+                        PH::template dit_wide<TL, false, T>(lines, a.twh, threadIdx.x, -1, sth);
+                    } else {
+                        constexpr int kBarC = 15;
+                        if (blockDim.x == 2 * TL) PH::template dit_wide<2 * TL, false, T>(lines, a.twh, threadIdx.x, kBarC, sth);
+                        else PH::template dit_blk<false, T>(lines, a.twh, threadIdx.x, blockDim.x, sth);
+                    }
+                    __syncthreads();
+                    for (int k = threadIdx.x; k < HX; k += blockDim.x) {
+                        const cx<T> A = lines[pidx(k)];
+                        const cx<T> B = cconj(lines[pidx(k == 0 ? 0 : NH - k)]);
+                        const cx<T> D = csub(A, B);
+                        const cx<T> E = cscale(cadd(A, B), (T)0.5);
+                        const cx<T> O = mk<T>((T)0.5 * D.y, (T)-0.5 * D.x);
+                        o0[k] = cadd(E, cmul(__ldg(&a.twr[k]), O));
+                    }
+                }
+            }
+            if (a.kind == 0 && !(HALF_OK && half)) {
                 fwd0([&](int k, cx<T> v) {
                     if (k < HX) o0[k] = v;
                 });
-            } else {
+            } else if (a.kind != 0) {
                 fwd0([&](int k, cx<T> v) { lines[pidx(k)] = v; });
                 __syncthreads();
                 cx<T>* o1 = out1 + (long long)zp * HX;

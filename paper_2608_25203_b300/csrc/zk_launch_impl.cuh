@@ -106,8 +106,6 @@ cudaError_t launch_row(int npx, int v, const RowArgs<T>& a, const cx<T>* tw, int
 template <typename T, int NPZ, int CB, int V, int DIV = 3>
 cudaError_t launch_col_t(const ColArgs<T>& a, const cx<T>* tw, cudaStream_t s, int* nblocks) {
     constexpr int TL = IPlan<NPZ, V>::TL;
-    constexpr int NZ = 2 * NPZ / DIV;
-    constexpr int LS = line_stride(NPZ);
     const int threads = CB * TL < 32 ? 32 : CB * TL;
     const int groups = threads / TL;
     const size_t smem = col_smem_bytes<T, NPZ, DIV>(a.kind == COL_FINAL, groups);
