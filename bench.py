@@ -206,8 +206,9 @@ def host_cpu():
 
 def oracle_threads():
     """Host threads the oracle's transforms use (scipy.fft workers)."""
-    from oracle import dft
-    return int(dft.WORKERS)
+    # the module, not the package's re-exported dft() function of the same name
+    from oracle.dft import WORKERS
+    return int(WORKERS)
 
 
 def cpu_baseline_rhs(eta, psi):

@@ -58,3 +58,9 @@ def test_reference_arm_other_ranks_exit_without_work():
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2",
                         "--steps", "1", "--warmup", "0"], env=env, capture_output=True, text=True, timeout=120)
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_oracle_threads_is_the_transform_worker_count():
+    # the cpu_baseline leg records how many host threads the oracle's transforms use
+    n = bench.oracle_threads()
+    assert isinstance(n, int) and 1 <= n <= (os.cpu_count() or 1)
