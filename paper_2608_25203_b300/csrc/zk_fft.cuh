@@ -36,6 +36,39 @@ template <typename T> using cx = typename CT<T>::type;
 template <typename T> __host__ __device__ __forceinline__ cx<T> mk(T a, T b) { cx<T> r; r.x = a; r.y = b; return r; }
 template <typename V> __host__ __device__ __forceinline__ V cadd(V a, V b) { a.x += b.x; a.y += b.y; return a; }
 template <typename V> __host__ __device__ __forceinline__ V csub(V a, V b) { a.x -= b.x; a.y -= b.y; return a; }
+// FP32 complex add and subtract as one packed instruction each (add/sub.rn.f32x2: two IEEE
+// round-to-nearest operations, the same results as the scalar pair); the butterflies issue
+// fewer instructions, which is what bounds the transforms.
+#ifdef __CUDA_ARCH__
+__device__ __forceinline__ unsigned long long f2_pack(float2 a) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
+    return r;
+}
+__device__ __forceinline__ float2 f2_unpack(unsigned long long r) {
+    float2 a;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(r));
+    return a;
+}
+#endif
+template <> __host__ __device__ __forceinline__ float2 cadd<float2>(float2 a, float2 b) {
+#ifdef __CUDA_ARCH__
+    unsigned long long r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2_pack(a)), "l"(f2_pack(b)));
+    return f2_unpack(r);
+#else
+    a.x += b.x; a.y += b.y; return a;
+#endif
+}
+template <> __host__ __device__ __forceinline__ float2 csub<float2>(float2 a, float2 b) {
+#ifdef __CUDA_ARCH__
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2_pack(a)), "l"(f2_pack(b)));
+    return f2_unpack(r);
+#else
+    a.x -= b.x; a.y -= b.y; return a;
+#endif
+}
 template <typename V, typename S> __host__ __device__ __forceinline__ V cscale(V a, S s) { a.x *= s; a.y *= s; return a; }
 template <typename V> __host__ __device__ __forceinline__ V cmul(V a, V b) {
     V r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r;
