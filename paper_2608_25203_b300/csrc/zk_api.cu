@@ -97,6 +97,7 @@ struct zk_ctx {
     long long fstride = 0;
     void *acc = nullptr;
     void *sfc = nullptr;       // surface planes eta, dx eta, dz eta: [3][npz][npx] real per tile
+    void *fsc = nullptr;       // final pass, split: transformed nonlinear parts Fe, Fp (2 compact per tile)
     void *stage = nullptr;
     void *tank = nullptr;      // two (nx/2) x (nz/2) FP64-sized arrays for tank I/O
     double *partial = nullptr;
@@ -440,6 +441,10 @@ struct Pipe {
             fin.nin = C(c->col) + (long long)F.npsi() * c->fstride;
             fin.s_eta = se;
             fin.s_psi = sp;
+            // Long columns: the update runs as its own launch over the compact spectra (the column
+            // kernel's one block per SM would wait on the stage state's global loads).
+            const bool split = c->fsc != nullptr && c->npz >= 1536 && fin.mode != FIN_ENERGY;
+            double b_epi = 0.0;
             {
                 // 2 products in, the stage state, then the epilogue's own traffic
                 double b = 2 * U + 2 * Cc;
@@ -453,10 +458,28 @@ struct Pipe {
                 case FIN_IRK4: b += 6 * Cc; break;                // y, ka read; y written
                 default: break;
                 }
+                if (split) {
+                    // transforms: products in, Fe and Fp out; update: Fe, Fp, the state and the rest
+                    b_epi = b - 2 * U + 2 * Cc;
+                    b = 2 * U + 2 * Cc;
+                }
                 note(c, s, ZK_K_COL_FINAL, b);
+            }
+            if (split) {
+                fin.split = 1;
+                fin.fe = reinterpret_cast<cx<T>*>(c->fsc);
+                fin.fp = fin.fe + (long long)c->nz * c->hx * c->nb;   // [tile][nz][hx] each
             }
             if ((e = launch_col<T>(c->npz, plan_of(c), c->col_ci, fin, twz, s, &c->fin_blocks)) != cudaSuccess) return e;
             ++nl;
+            if (split) {
+                note(c, s, ZK_K_COL_FINAL, b_epi);
+                const long long n = (long long)c->nz * c->hx;
+                const int blocks = (int)std::min<long long>((n + 255) / 256, 148LL * 16);
+                fin_epilogue_kernel<T><<<dim3(blocks, std::max(1, c->nb)), 256, 0, s>>>(fin);
+                if ((e = cudaGetLastError()) != cudaSuccess) return e;
+                ++nl;
+            }
         }
         if (nlaunch) *nlaunch += nl;
         return cudaSuccess;
@@ -1007,6 +1030,7 @@ zk_status ctx_create(zk_ctx** out, int nx, int nz, double Lx, double Lz, const d
     // 8 bytes per element in every precision, so FP32 contexts can switch on FP64 series sums
     if (st == ZK_OK) st = dalloc(c, &c->acc, (size_t)c->tacc * 8 * nb);
     if (st == ZK_OK && M >= 2) st = dalloc(c, &c->sfc, (size_t)3 * c->tacc * rsz * nb);
+    if (st == ZK_OK && c->npz >= 1536) st = dalloc(c, &c->fsc, 2 * compact);
     if (st == ZK_OK) st = dalloc(c, &c->stage, (size_t)2 * nx * nz * kIoElem);
     if (st == ZK_OK) st = dalloc(c, &c->tank, (size_t)2 * (nx / 2) * (nz / 2) * 8);
     c->npartial = c->hx * nb;              // at most one column-kernel block per column

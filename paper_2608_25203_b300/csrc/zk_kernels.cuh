@@ -141,6 +141,11 @@ struct ColArgs {
     const T* hb;                    // nullptr: every tile has depth h
     int nb;                         // tiles in the launch (host side: grid.y)
     int pad3;                       // host side: 3N padding (kernels with DIV = 6)
+    // kind 2: split = 1 stores the transformed nonlinear parts (Fe, Fp) to fe / fp (compact)
+    // and leaves the update to fin_epilogue_kernel
+    int split;
+    cx<T>* fe;
+    cx<T>* fp;
 };
 
 static __global__ void energy_finalize_kernel(const double* __restrict__ partial, int n, double* __restrict__ out) {

@@ -407,6 +407,160 @@ __device__ __forceinline__ void col2_store_tile(const cx<T>* sm, int per, cx<T>*
     }
 }
 
+// The final pass's update of one kept mode (kx index col, kz index mz) at compact index idx:
+// the right-hand side from the transformed nonlinear parts Fe, Fp (scaled and tapered; Fe is
+// zero at k = 0) and the linear parts G0 psi_hat, -g eta_hat, then the mode's epilogue (RK4
+// stage combination with the Eq. 17 filter at the last stage, IF-AB2 of Eqs. 15-16, IF-RK4,
+// the right-hand side itself, the inverse DNO update of Eq. 19, or the FP64 energy sums).
+template <typename T>
+__device__ __forceinline__ void fin_mode(const ColArgs<T>& a, long long idx, int col, int mz, cx<T> Fe, cx<T> Fp,
+                                         T hh, T ihx, T inz2, double& e_kin, double& e_pot, double& e_bad) {
+    const T kxc = a.kx0 * (T)col;
+    const T kz = a.kz0 * (T)mz;
+    const T k = d_kabs(kxc * kxc + kz * kz);
+    const cx<T> se = a.s_eta[idx], sp = a.s_psi[idx];
+    const T G0 = k * tanh_kh(k * hh);
+    cx<T> de = cadd(cscale(sp, G0), Fe);
+    if (col == 0 && mz == 0) de = mk<T>(0, 0);
+    const cx<T> dp = cadd(cscale(se, -a.g), Fp);
+    switch (a.mode) {
+    case FIN_INVDNO: {
+        // Eq. 19: psi <- G0^{-1} (v - [G(eta) - G0] psi); the k = 0 mode keeps its value
+        if (!(col == 0 && mz == 0)) a.y_psi[idx] = cscale(csub(a.v_hat[idx], Fe), (T)1 / G0);
+    } break;
+    case FIN_IFAB2: {
+        // Eqs. 15-16: exact linear rotation plus the Duhamel response to the
+        // AB2-extrapolated forcing F* (IF-Euler at the first step).
+        cx<T> Fse = Fe, Fsp = Fp;
+        if (!a.ab_first) {
+            Fse = csub(cscale(Fe, (T)1.5), cscale(a.h_eta[idx], (T)0.5));
+            Fsp = csub(cscale(Fp, (T)1.5), cscale(a.h_psi[idx], (T)0.5));
+        }
+        a.h_eta[idx] = Fe;
+        a.h_psi[idx] = Fp;
+        const T w = d_sqrt(a.g * G0);
+        T c, sw, G0sw, gsw, omc_g, omc_G0;
+        if (w > (T)0) {
+            T sh, ch;                              // half angle: one sincos gives both
+            d_sincos((T)0.5 * w * a.dt, &sh, &ch);
+            const T omc = (T)2 * sh * sh;          // 1 - cos(w dt) without cancellation
+            c = (T)1 - omc;
+            sw = (T)2 * sh * ch / w;               // sin(w dt) / w
+            G0sw = G0 * sw;                        // (G0 / w) sin(w dt)
+            gsw = a.g * sw;                        // (g / w) sin(w dt)
+            omc_g = omc / a.g;
+            omc_G0 = omc / G0;
+        } else {                                   // k = 0 limits stated under Eq. 16
+            c = 1; sw = a.dt; G0sw = 0; gsw = a.g * a.dt; omc_g = 0; omc_G0 = (T)0.5 * a.g * a.dt * a.dt;
+        }
+        cx<T> e1 = cadd(cadd(cscale(se, c), cscale(sp, G0sw)), cadd(cscale(Fse, sw), cscale(Fsp, omc_g)));
+        cx<T> p1 = cadd(csub(cscale(sp, c), cscale(se, gsw)), csub(cscale(Fsp, sw), cscale(Fse, omc_G0)));
+        if (a.filter) {
+            const T rx = (T)col * ihx;
+            const T rz = (T)(mz < 0 ? -mz : mz) * inz2;
+            const T A = (T)0.125 * ((T)5 + (T)4 * d_cospi(rx) - d_cospi((T)2 * rx)) *
+                        ((T)0.125 * ((T)5 + (T)4 * d_cospi(rz) - d_cospi((T)2 * rz)));
+            e1 = cscale(e1, A);
+            p1 = cscale(p1, A);
+        }
+        a.y_eta[idx] = e1;
+        a.y_psi[idx] = p1;
+    } break;
+    case FIN_RHS:
+        a.ko_eta[idx] = de; a.ko_psi[idx] = dp;
+        break;
+    case FIN_IRK1:
+    case FIN_IRK2:
+    case FIN_IRK3:
+    case FIN_IRK4: {
+        // Integrating-factor RK4 (Lawson): the linear flow E_t of Eq. 14 exactly, RK4 on
+        // the nonlinear part k = (Fe, Fp) of this stage in the rotating frame.
+        const T w = d_sqrt(a.g * G0);
+        T c1, s1, c2, s2;                          // cos and sin/w of w h/2 and of w h
+        if (w > (T)0) {
+            T sh, ch;
+            d_sincos((T)0.5 * w * a.dt, &sh, &ch);
+            c1 = ch; s1 = sh / w;
+            c2 = (T)1 - (T)2 * sh * sh; s2 = (T)2 * sh * ch / w;
+        } else {                                   // k = 0: E_t (e, p) = (e, p - g t e)
+            c1 = 1; s1 = (T)0.5 * a.dt; c2 = 1; s2 = a.dt;
+        }
+        auto rot_e = [&](cx<T> e, cx<T> pp, T c, T sw) { return cadd(cscale(e, c), cscale(pp, G0 * sw)); };
+        auto rot_p = [&](cx<T> e, cx<T> pp, T c, T sw) { return csub(cscale(pp, c), cscale(e, a.g * sw)); };
+        const T hh = a.dt;
+        const cx<T> ye = a.y_eta[idx], yp = a.y_psi[idx];
+        if (a.mode == FIN_IRK1) {
+            a.ka_eta[idx] = rot_e(Fe, Fp, c2, s2);
+            a.ka_psi[idx] = rot_p(Fe, Fp, c2, s2);
+            const cx<T> ue = cadd(ye, cscale(Fe, (T)0.5 * hh)), up = cadd(yp, cscale(Fp, (T)0.5 * hh));
+            a.ys_eta[idx] = rot_e(ue, up, c1, s1);
+            a.ys_psi[idx] = rot_p(ue, up, c1, s1);
+        } else if (a.mode == FIN_IRK2) {
+            a.ka_eta[idx] = cadd(a.ka_eta[idx], cscale(rot_e(Fe, Fp, c1, s1), (T)2));
+            a.ka_psi[idx] = cadd(a.ka_psi[idx], cscale(rot_p(Fe, Fp, c1, s1), (T)2));
+            a.ys_eta[idx] = cadd(rot_e(ye, yp, c1, s1), cscale(Fe, (T)0.5 * hh));
+            a.ys_psi[idx] = cadd(rot_p(ye, yp, c1, s1), cscale(Fp, (T)0.5 * hh));
+        } else if (a.mode == FIN_IRK3) {
+            const cx<T> ke = rot_e(Fe, Fp, c1, s1), kp = rot_p(Fe, Fp, c1, s1);
+            a.ka_eta[idx] = cadd(a.ka_eta[idx], cscale(ke, (T)2));
+            a.ka_psi[idx] = cadd(a.ka_psi[idx], cscale(kp, (T)2));
+            a.ys_eta[idx] = cadd(rot_e(ye, yp, c2, s2), cscale(ke, hh));
+            a.ys_psi[idx] = cadd(rot_p(ye, yp, c2, s2), cscale(kp, hh));
+        } else {
+            T A = 1;
+            if (a.filter) {
+                const T rx = (T)col * ihx;
+                const T rz = (T)(mz < 0 ? -mz : mz) * inz2;
+                A = (T)0.125 * ((T)5 + (T)4 * d_cospi(rx) - d_cospi((T)2 * rx)) *
+                    ((T)0.125 * ((T)5 + (T)4 * d_cospi(rz) - d_cospi((T)2 * rz)));
+            }
+            const T w6 = hh / (T)6;
+            const cx<T> ne = cadd(rot_e(ye, yp, c2, s2), cscale(cadd(a.ka_eta[idx], Fe), w6));
+            const cx<T> np = cadd(rot_p(ye, yp, c2, s2), cscale(cadd(a.ka_psi[idx], Fp), w6));
+            a.y_eta[idx] = cscale(ne, A);
+            a.y_psi[idx] = cscale(np, A);
+        }
+    } break;
+    case FIN_RK1: {
+        a.ka_eta[idx] = de; a.ka_psi[idx] = dp;
+        const T hd = (T)0.5 * a.dt;
+        a.ys_eta[idx] = cadd(a.y_eta[idx], cscale(de, hd));
+        a.ys_psi[idx] = cadd(a.y_psi[idx], cscale(dp, hd));
+    } break;
+    case FIN_RK2:
+    case FIN_RK3: {
+        a.ka_eta[idx] = cadd(a.ka_eta[idx], cscale(de, (T)2));
+        a.ka_psi[idx] = cadd(a.ka_psi[idx], cscale(dp, (T)2));
+        const T hd = a.mode == FIN_RK2 ? (T)0.5 * a.dt : a.dt;
+        a.ys_eta[idx] = cadd(a.y_eta[idx], cscale(de, hd));
+        a.ys_psi[idx] = cadd(a.y_psi[idx], cscale(dp, hd));
+    } break;
+    case FIN_RK4: {
+        const T w = a.dt / (T)6;
+        T A = 1;
+        if (a.filter) {
+            const T rx = (T)col * ihx;
+            const T rz = (T)(mz < 0 ? -mz : mz) * inz2;
+            A = (T)0.125 * ((T)5 + (T)4 * d_cospi(rx) - d_cospi((T)2 * rx)) *
+                ((T)0.125 * ((T)5 + (T)4 * d_cospi(rz) - d_cospi((T)2 * rz)));
+        }
+        const cx<T> ye = cadd(a.y_eta[idx], cscale(cadd(a.ka_eta[idx], de), w));
+        const cx<T> yp = cadd(a.y_psi[idx], cscale(cadd(a.ka_psi[idx], dp), w));
+        a.y_eta[idx] = cscale(ye, A);
+        a.y_psi[idx] = cscale(yp, A);
+    } break;
+    case FIN_ENERGY: {
+        const double wgt = col == 0 ? 1.0 : 2.0;
+        e_kin += wgt * ((double)sp.x * (double)de.x + (double)sp.y * (double)de.y);
+        e_pot += wgt * ((double)se.x * (double)se.x + (double)se.y * (double)se.y);
+        const bool fin = isfinite((double)se.x) && isfinite((double)se.y) &&
+                         isfinite((double)sp.x) && isfinite((double)sp.y);
+        if (!fin) e_bad += 1.0;
+    } break;
+    default: break;
+    }
+}
+
 // Where the final pass's two lines per column leave room for a single block per SM (over half
 // of the SM's shared memory), say so to the compiler: it may then use the registers that
 // occupancy leaves free instead of spilling. 0 leaves the minimum unspecified.
@@ -515,7 +669,7 @@ col2_kernel(const ColArgs<T> a, const cx<T>* __restrict__ tw) {
     // DRAM: request this tile's rows into L2 now, so that the fetch overlaps the tile load and
     // the two transforms (one prefetch per 32-byte sector, the addresses the epilogue reads).
     // Grids below 1024 points per axis keep their state in L2: no prefetch there.
-    if constexpr (NPZ >= 1536) {
+    if (NPZ >= 1536 && !a.split) {
         const cx<T>* pf[6] = {a.s_eta, a.s_psi, nullptr, nullptr, nullptr, nullptr};
         int npf = 2;
         if (a.mode >= FIN_RK1 && a.mode <= FIN_RK4) {
@@ -547,161 +701,26 @@ col2_kernel(const ColArgs<T> a, const cx<T>* __restrict__ tw) {
         if (col >= a.hx) continue;
         const long long idx = os + (long long)ic * a.hx + col;
         if (ic == NZ / 2) {
-            if (a.mode == FIN_RHS) { a.ko_eta[idx] = mk<T>(0, 0); a.ko_psi[idx] = mk<T>(0, 0); }
+            if (a.mode == FIN_RHS && !a.split) { a.ko_eta[idx] = mk<T>(0, 0); a.ko_psi[idx] = mk<T>(0, 0); }
             continue;
         }
         const int mz = ic < NZ / 2 ? ic : ic - NZ;
         const int ip = mz >= 0 ? mz : mz + NPZ;
         const T kxc = a.kx0 * (T)col;
         const T kz = a.kz0 * (T)mz;
-        const T k = d_kabs(kxc * kxc + kz * kz);
         T s = a.fscale;
         if (a.taper) s *= d_taper((kxc * kxc + kz * kz) * ikc2);
         const cx<T>* lc = sm + (size_t)cg * PER;
         cx<T> Fe = cscale(lc[pidx(ip)], s);
         const cx<T> Fp = cscale(lc[LS + pidx(ip)], s);
-        const cx<T> se = a.s_eta[idx], sp = a.s_psi[idx];
-        const T G0 = k * tanh_kh(k * hh);
         if (col == 0 && mz == 0) Fe = mk<T>(0, 0);   // d eta/dt has zero mean
-        cx<T> de = cadd(cscale(sp, G0), Fe);
-        if (col == 0 && mz == 0) de = mk<T>(0, 0);
-        const cx<T> dp = cadd(cscale(se, -a.g), Fp);
-        switch (a.mode) {
-        case FIN_INVDNO: {
-            // Eq. 19: psi <- G0^{-1} (v - [G(eta) - G0] psi); the k = 0 mode keeps its value
-            if (!(col == 0 && mz == 0)) a.y_psi[idx] = cscale(csub(a.v_hat[idx], Fe), (T)1 / G0);
-        } break;
-        case FIN_IFAB2: {
-            // Eqs. 15-16: exact linear rotation plus the Duhamel response to the
-            // AB2-extrapolated forcing F* (IF-Euler at the first step).
-            cx<T> Fse = Fe, Fsp = Fp;
-            if (!a.ab_first) {
-                Fse = csub(cscale(Fe, (T)1.5), cscale(a.h_eta[idx], (T)0.5));
-                Fsp = csub(cscale(Fp, (T)1.5), cscale(a.h_psi[idx], (T)0.5));
-            }
-            a.h_eta[idx] = Fe;
-            a.h_psi[idx] = Fp;
-            const T w = d_sqrt(a.g * G0);
-            T c, sw, G0sw, gsw, omc_g, omc_G0;
-            if (w > (T)0) {
-                T sh, ch;                              // half angle: one sincos gives both
-                d_sincos((T)0.5 * w * a.dt, &sh, &ch);
-                const T omc = (T)2 * sh * sh;          // 1 - cos(w dt) without cancellation
-                c = (T)1 - omc;
-                sw = (T)2 * sh * ch / w;               // sin(w dt) / w
-                G0sw = G0 * sw;                        // (G0 / w) sin(w dt)
-                gsw = a.g * sw;                        // (g / w) sin(w dt)
-                omc_g = omc / a.g;
-                omc_G0 = omc / G0;
-            } else {                                   // k = 0 limits stated under Eq. 16
-                c = 1; sw = a.dt; G0sw = 0; gsw = a.g * a.dt; omc_g = 0; omc_G0 = (T)0.5 * a.g * a.dt * a.dt;
-            }
-            cx<T> e1 = cadd(cadd(cscale(se, c), cscale(sp, G0sw)), cadd(cscale(Fse, sw), cscale(Fsp, omc_g)));
-            cx<T> p1 = cadd(csub(cscale(sp, c), cscale(se, gsw)), csub(cscale(Fsp, sw), cscale(Fse, omc_G0)));
-            if (a.filter) {
-                const T rx = (T)col * ihx;
-                const T rz = (T)(mz < 0 ? -mz : mz) * inz2;
-                const T A = (T)0.125 * ((T)5 + (T)4 * d_cospi(rx) - d_cospi((T)2 * rx)) *
-                            ((T)0.125 * ((T)5 + (T)4 * d_cospi(rz) - d_cospi((T)2 * rz)));
-                e1 = cscale(e1, A);
-                p1 = cscale(p1, A);
-            }
-            a.y_eta[idx] = e1;
-            a.y_psi[idx] = p1;
-        } break;
-        case FIN_RHS:
-            a.ko_eta[idx] = de; a.ko_psi[idx] = dp;
-            break;
-        case FIN_IRK1:
-        case FIN_IRK2:
-        case FIN_IRK3:
-        case FIN_IRK4: {
-            // Integrating-factor RK4 (Lawson): the linear flow E_t of Eq. 14 exactly, RK4 on
-            // the nonlinear part k = (Fe, Fp) of this stage in the rotating frame.
-            const T w = d_sqrt(a.g * G0);
-            T c1, s1, c2, s2;                          // cos and sin/w of w h/2 and of w h
-            if (w > (T)0) {
-                T sh, ch;
-                d_sincos((T)0.5 * w * a.dt, &sh, &ch);
-                c1 = ch; s1 = sh / w;
-                c2 = (T)1 - (T)2 * sh * sh; s2 = (T)2 * sh * ch / w;
-            } else {                                   // k = 0: E_t (e, p) = (e, p - g t e)
-                c1 = 1; s1 = (T)0.5 * a.dt; c2 = 1; s2 = a.dt;
-            }
-            auto rot_e = [&](cx<T> e, cx<T> pp, T c, T sw) { return cadd(cscale(e, c), cscale(pp, G0 * sw)); };
-            auto rot_p = [&](cx<T> e, cx<T> pp, T c, T sw) { return csub(cscale(pp, c), cscale(e, a.g * sw)); };
-            const T hh = a.dt;
-            const cx<T> ye = a.y_eta[idx], yp = a.y_psi[idx];
-            if (a.mode == FIN_IRK1) {
-                a.ka_eta[idx] = rot_e(Fe, Fp, c2, s2);
-                a.ka_psi[idx] = rot_p(Fe, Fp, c2, s2);
-                const cx<T> ue = cadd(ye, cscale(Fe, (T)0.5 * hh)), up = cadd(yp, cscale(Fp, (T)0.5 * hh));
-                a.ys_eta[idx] = rot_e(ue, up, c1, s1);
-                a.ys_psi[idx] = rot_p(ue, up, c1, s1);
-            } else if (a.mode == FIN_IRK2) {
-                a.ka_eta[idx] = cadd(a.ka_eta[idx], cscale(rot_e(Fe, Fp, c1, s1), (T)2));
-                a.ka_psi[idx] = cadd(a.ka_psi[idx], cscale(rot_p(Fe, Fp, c1, s1), (T)2));
-                a.ys_eta[idx] = cadd(rot_e(ye, yp, c1, s1), cscale(Fe, (T)0.5 * hh));
-                a.ys_psi[idx] = cadd(rot_p(ye, yp, c1, s1), cscale(Fp, (T)0.5 * hh));
-            } else if (a.mode == FIN_IRK3) {
-                const cx<T> ke = rot_e(Fe, Fp, c1, s1), kp = rot_p(Fe, Fp, c1, s1);
-                a.ka_eta[idx] = cadd(a.ka_eta[idx], cscale(ke, (T)2));
-                a.ka_psi[idx] = cadd(a.ka_psi[idx], cscale(kp, (T)2));
-                a.ys_eta[idx] = cadd(rot_e(ye, yp, c2, s2), cscale(ke, hh));
-                a.ys_psi[idx] = cadd(rot_p(ye, yp, c2, s2), cscale(kp, hh));
-            } else {
-                T A = 1;
-                if (a.filter) {
-                    const T rx = (T)col * ihx;
-                    const T rz = (T)(mz < 0 ? -mz : mz) * inz2;
-                    A = (T)0.125 * ((T)5 + (T)4 * d_cospi(rx) - d_cospi((T)2 * rx)) *
-                        ((T)0.125 * ((T)5 + (T)4 * d_cospi(rz) - d_cospi((T)2 * rz)));
-                }
-                const T w6 = hh / (T)6;
-                const cx<T> ne = cadd(rot_e(ye, yp, c2, s2), cscale(cadd(a.ka_eta[idx], Fe), w6));
-                const cx<T> np = cadd(rot_p(ye, yp, c2, s2), cscale(cadd(a.ka_psi[idx], Fp), w6));
-                a.y_eta[idx] = cscale(ne, A);
-                a.y_psi[idx] = cscale(np, A);
-            }
-        } break;
-        case FIN_RK1: {
-            a.ka_eta[idx] = de; a.ka_psi[idx] = dp;
-            const T hd = (T)0.5 * a.dt;
-            a.ys_eta[idx] = cadd(a.y_eta[idx], cscale(de, hd));
-            a.ys_psi[idx] = cadd(a.y_psi[idx], cscale(dp, hd));
-        } break;
-        case FIN_RK2:
-        case FIN_RK3: {
-            a.ka_eta[idx] = cadd(a.ka_eta[idx], cscale(de, (T)2));
-            a.ka_psi[idx] = cadd(a.ka_psi[idx], cscale(dp, (T)2));
-            const T hd = a.mode == FIN_RK2 ? (T)0.5 * a.dt : a.dt;
-            a.ys_eta[idx] = cadd(a.y_eta[idx], cscale(de, hd));
-            a.ys_psi[idx] = cadd(a.y_psi[idx], cscale(dp, hd));
-        } break;
-        case FIN_RK4: {
-            const T w = a.dt / (T)6;
-            T A = 1;
-            if (a.filter) {
-                const T rx = (T)col * ihx;
-                const T rz = (T)(mz < 0 ? -mz : mz) * inz2;
-                A = (T)0.125 * ((T)5 + (T)4 * d_cospi(rx) - d_cospi((T)2 * rx)) *
-                    ((T)0.125 * ((T)5 + (T)4 * d_cospi(rz) - d_cospi((T)2 * rz)));
-            }
-            const cx<T> ye = cadd(a.y_eta[idx], cscale(cadd(a.ka_eta[idx], de), w));
-            const cx<T> yp = cadd(a.y_psi[idx], cscale(cadd(a.ka_psi[idx], dp), w));
-            a.y_eta[idx] = cscale(ye, A);
-            a.y_psi[idx] = cscale(yp, A);
-        } break;
-        case FIN_ENERGY: {
-            const double wgt = col == 0 ? 1.0 : 2.0;
-            e_kin += wgt * ((double)sp.x * (double)de.x + (double)sp.y * (double)de.y);
-            e_pot += wgt * ((double)se.x * (double)se.x + (double)se.y * (double)se.y);
-            const bool fin = isfinite((double)se.x) && isfinite((double)se.y) &&
-                             isfinite((double)sp.x) && isfinite((double)sp.y);
-            if (!fin) e_bad += 1.0;
-        } break;
-        default: break;
+        if (a.split) {
+            // the update runs in fin_epilogue_kernel, over the compact spectra
+            a.fe[idx] = Fe;
+            a.fp[idx] = Fp;
+            continue;
         }
+        fin_mode(a, idx, col, mz, Fe, Fp, hh, ihx, inz2, e_kin, e_pot, e_bad);
     }
     if (a.mode == FIN_ENERGY) {
         __shared__ double red[3][16];
@@ -726,6 +745,30 @@ col2_kernel(const ColArgs<T> a, const cx<T>* __restrict__ tw) {
 }
 
 
+
+// The final pass's update as its own launch over the compact spectra (consecutive threads
+// take consecutive kx of one kz row): the column kernel then ends with its transforms and the
+// update, which waits on the stage state in global memory, runs with every warp of the SM.
+// Same arithmetic as the fused epilogue of col2_kernel. Not for FIN_ENERGY (block partials).
+template <typename T>
+__global__ void __launch_bounds__(256) fin_epilogue_kernel(const ColArgs<T> a) {
+    const int nz = a.nz_grid;
+    const long long n = (long long)nz * a.hx;
+    const long long os = (long long)blockIdx.y * a.tst;
+    const T hh = a.hb ? a.hb[blockIdx.y] : a.h;
+    const T ihx = (T)1 / (T)a.hx, inz2 = (T)1 / (T)(nz / 2);
+    double e_kin = 0.0, e_pot = 0.0, e_bad = 0.0;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const int ic = (int)(e / a.hx), col = (int)(e - (long long)ic * a.hx);
+        const long long idx = os + e;
+        if (ic == nz / 2) {
+            if (a.mode == FIN_RHS) { a.ko_eta[idx] = mk<T>(0, 0); a.ko_psi[idx] = mk<T>(0, 0); }
+            continue;
+        }
+        const int mz = ic < nz / 2 ? ic : ic - nz;
+        fin_mode(a, idx, col, mz, a.fe[idx], a.fp[idx], hh, ihx, inz2, e_kin, e_pot, e_bad);
+    }
+}
 
 // ---------------------------------------------------------------------------
 // Learned closure: features in, residual out (compact spectra [nz][hx]).
