@@ -5,6 +5,8 @@
 //   col(kind 0) -> [row(r) -> col(kind 1, r)] for r = 1..M-1 -> row(final) -> col(final)
 // An RK4 step is four of them; the final column kernel of each stage does the
 // stage combination, and the last one also applies the state filter (Eq. 17).
+// On 1536-point and longer columns the final column kernel ends with its
+// transforms and a separate update launch (fin_epilogue_kernel) does the rest.
 // zk_step captures the launches of one step into a CUDA graph (re-captured
 // when dt or the options change) and replays it n times on the context's
 // stream.

@@ -1,5 +1,5 @@
 """The final column pass with its update as a separate launch (lines of 1536 points and more)
-against the FP64 oracle, in every update mode.
+against the FP64 oracle, in every update mode, and the paper's IF-AB2 at the sea workload's size.
 
 At 1024^2 (1536-point padded columns) the final column kernel stores the transformed nonlinear
 parts and fin_epilogue_kernel applies the update over the compact spectra. In an FP64 context
@@ -96,3 +96,26 @@ def test_dno_inverse(zk, case):
     _, gp = s.get_state()
     s.close()
     assert rel(gp, want) < 1e-11
+
+
+def test_ifab2_fp32_at_2048(zk):
+    # the sea workload's grid (3072-point rows and columns: surface planes, half-length forward
+    # transform, split final pass) in FP32, two IF-AB2 steps against the oracle from the same
+    # FP32-rounded state. Bar: 4 n 2^-24 for the n steps (the stepped FP32 bar of the parity
+    # tests) plus the state conversions on the unpadded grid, a forward transform at set_state
+    # and an inverse one at get_state, each O(log2(nx nz)) roundings: (4 n + 2 log2(nx nz)) 2^-24
+    n, L, h = 2048, 1600.0, 50.0
+    e, p, _ = seas.jonswap_sea(n, n, L, L, h, 4.0, 12.0, 3)
+    e, p = e.astype(np.float32), p.astype(np.float32)
+    o = Oracle(Grid(n, n, L, L, h), 5, eps=0.5)
+    eh, ph = o.spectrum(e.astype(np.float64)), o.spectrum(p.astype(np.float64))
+    we, wp, hist = o.step_ifab2(eh, ph, DT)
+    we, wp, _ = o.step_ifab2(we, wp, DT, hist)
+    s = zk.Zakharov(n, n, L, L, h, M=5, eps=0.5)
+    zk.zk_set_options(s.ctx, eps=0.5, integrator=zk.ZK_IFAB2)
+    s.set_state(e, p)
+    s.step(DT, 2)
+    ge, gp = s.get_state()
+    s.close()
+    bar = (4 * 2 + 2 * np.log2(n * n)) * 2.0 ** -24
+    assert rel(ge, o.physical(we)) < bar and rel(gp, o.physical(wp)) < bar, (rel(ge, o.physical(we)), rel(gp, o.physical(wp)))
