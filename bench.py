@@ -408,8 +408,8 @@ def closure_arm(args):
     net, losses = ct.train(X[:-nv], T[:-nv], ins, outs, iters=3000, batch=8, lr=1e-3, lr_end=1e-5, log_every=500)
     torch.cuda.synchronize()
     t_train = time.time() - t0
-    Xv /= torch.as_tensor(ins, device="cuda")[None, :, None, None]
-    Tv /= torch.as_tensor(outs, device="cuda")[None, :, None, None]
+    ct.apply_scales(Xv, ins)
+    ct.apply_scales(Tv, outs)
     val = ct.validation_loss(net, Xv, Tv)
     del X, T, Xv, Tv
     torch.cuda.empty_cache()
@@ -423,6 +423,7 @@ def closure_arm(args):
             s.set_state(e32, p32)
             if closure:
                 zk.zk_closure_set(s.ctx, net.n, 2, ins, outs, check_every=closure[0], check_tol=closure[1])
+                zk.zk_closure_set_once_per_step(s.ctx, closure[2])
 
         start()
         s.step(dt, 3)                      # graph capture and warm-up, then restart
@@ -453,7 +454,9 @@ def closure_arm(args):
             for M in (2, 3, 4, 5):
                 o, ms, _ = run(n, L, M, seed)
                 row[f"M{M}"] = {"ms": ms, "err": {k: float(np.linalg.norm(o[k] - ref[k]) / np.linalg.norm(ref[k])) for k in o}}
-            for name, cfg in (("M2+net", (50, 0.2)), ("M2+net_nocheck", (0, 1.0))):
+            # the network at every RK stage (check on / off), and once per step (check off)
+            for name, cfg in (("M2+net", (50, 0.2, 0)), ("M2+net_nocheck", (0, 1.0, 0)),
+                              ("M2+net_once_nocheck", (0, 1.0, 1))):
                 o, ms, st = run(n, L, 2, seed, closure=cfg)
                 row[name] = {"ms": ms, "status": st,
                              "err": {k: float(np.linalg.norm(o[k] - ref[k]) / np.linalg.norm(ref[k])) for k in o}}
@@ -468,8 +471,13 @@ def closure_arm(args):
         pts.sort()
         le = np.log([p[0] for p in pts])
         cost_at = float(np.interp(np.log(learned_err), le, [p[1] for p in pts]))
+        once_err = float(np.mean([per[s]["M2+net_once_nocheck"]["err"][last] for s in per]))
+        once_ms = float(np.mean([per[s]["M2+net_once_nocheck"]["ms"] for s in per]))
+        once_cost_at = float(np.interp(np.log(once_err), le, [p[1] for p in pts]))
         results[n] = {"seeds": per, "learned_err": learned_err, "learned_ms": learned_ms,
-                      "plain_ms_at_learned_err": cost_at, "ratio": cost_at / learned_ms}
+                      "plain_ms_at_learned_err": cost_at, "ratio": cost_at / learned_ms,
+                      "once_per_step": {"err": once_err, "ms": once_ms, "plain_ms_at_err": once_cost_at,
+                                        "ratio": once_cost_at / once_ms}}
     print(json.dumps({
         "metric": "learned closure: plain-series cost at equal eta error / closure cost (2048^2)",
         "value": results[2048]["ratio"], "unit": "x", "higher_is_better": True, "steps": steps, "dtype": "f32",

@@ -376,6 +376,16 @@ zk_status zk_net_adam(zk_net *n, const float *grad, double lr, void *stream);
  * one Adam step; *loss (may be NULL) receives the loss before the update. */
 zk_status zk_net_train_step(zk_net *n, const float *x, const float *target, int batch, int nz, int nx, double lr,
                             double *loss, void *stream);
+/* Data preparation of the closure's training set (the network's per-channel input and output
+ * scales). x: device FP32 array [n][c][hw] (n samples, c <= 64 channels of hw values each).
+ * zk_net_channel_rms: rms[ch] = sqrt(mean over samples and positions of x^2), into host memory
+ * rms[c]; FP64 sums in a fixed order (the same result on every call).
+ * zk_net_scale_channels: x[smp][ch][:] *= mul[ch] in place, mul a host array of c factors.
+ * Both queue on `stream` and synchronise it before returning; their few scratch bytes come
+ * from the stream-ordered allocator. ZK_EINVAL for bad sizes or NULL pointers, ZK_ENOMEM,
+ * ZK_ECUDA. */
+zk_status zk_net_channel_rms(const float *x, long long n, int c, int hw, float *rms, void *stream);
+zk_status zk_net_scale_channels(float *x, long long n, int c, int hw, const float *mul, void *stream);
 /* Inference engine of the network (used by zk_net_predict and by an attached
  * closure): mode 0 = the FP32 SIMT kernels above; mode 1 (the default) = 5th-generation
  * tensor cores (tcgen05 MMAs with FP32 accumulators in TMEM; the same FP16
@@ -408,6 +418,12 @@ zk_status zk_closure_features(zk_ctx *ctx, int base_order, const float *in_scale
  * attached. */
 zk_status zk_closure_set(zk_ctx *ctx, zk_net *net, int base_order, const float *in_scale, const float *out_scale,
                          int check_every, double check_tol);
+/* How often the closure's network is evaluated in an RK4 step: on = 0 (default) at every
+ * stage's state; on = 1 at the first stage only, its residual spectrum then applied again at
+ * stages 2-4 (a quarter of the network's cost; the correction lags the stage states by up to
+ * one step). The base-order right-hand side is still evaluated at every stage. ZK_EINVAL for
+ * other values. */
+zk_status zk_closure_set_once_per_step(zk_ctx *ctx, int on);
 /* active: 1 while the closure is in use; checks made; the step count at which
  * it fell back (-1: never); the error of the last check (-1: none yet). */
 zk_status zk_closure_status(const zk_ctx *ctx, int *active, int *checks, long long *fallback_step, double *last_err);

@@ -190,3 +190,20 @@ class ClosureOracle(Oracle):
         de, dp = super().rhs(eh, ph)
         Re, Rp = self.residual_hat(eh, ph)
         return de + Re, dp + Rp
+
+    def step_rk4_frozen(self, eh, ph, dt):
+        """Classical RK4 in which the network's residual is evaluated once, at the step's start
+        state, and added to the base-order right-hand side of every stage; then the filter."""
+        Re, Rp = self.residual_hat(eh, ph)
+
+        def f(e, p):
+            de, dp = Oracle.rhs(self, e, p)
+            return de + Re, dp + Rp
+
+        k1e, k1p = f(eh, ph)
+        k2e, k2p = f(eh + 0.5 * dt * k1e, ph + 0.5 * dt * k1p)
+        k3e, k3p = f(eh + 0.5 * dt * k2e, ph + 0.5 * dt * k2p)
+        k4e, k4p = f(eh + dt * k3e, ph + dt * k3p)
+        eh = eh + dt / 6.0 * (k1e + 2 * k2e + 2 * k3e + k4e)
+        ph = ph + dt / 6.0 * (k1p + 2 * k2p + 2 * k3p + k4p)
+        return self.apply_filter(eh, ph)

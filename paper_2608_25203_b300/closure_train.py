@@ -72,17 +72,22 @@ def make_dataset(seeds, n=512, L=400.0, h=30.0, eps=0.5, dt=0.02, M=6, base=2, s
 
 
 def channel_scales(X, T):
-    """RMS of every feature and target channel over the data set."""
-    xs = X.pow(2).mean(dim=(0, 2, 3)).sqrt().cpu().numpy().astype(np.float32)
-    ts = T.pow(2).mean(dim=(0, 2, 3)).sqrt().cpu().numpy().astype(np.float32)
+    """RMS of every feature and target channel over the data set (library reduction, FP64 sums)."""
+    xs = zk.zk_net_channel_rms(X)
+    ts = zk.zk_net_channel_rms(T)
     return np.maximum(xs, 1e-30), np.maximum(ts, 1e-30)
+
+
+def apply_scales(X, scale):
+    """Divide every channel of X by its scale, in place (library kernel)."""
+    zk.zk_net_scale_channels(X, (1.0 / np.asarray(scale, np.float64)).astype(np.float32))
 
 
 def train(X, T, in_scale, out_scale, iters=2000, batch=4, lr=2e-3, lr_end=2e-4, seed=0, log_every=0, net=None):
     """Train a network on the scaled data; returns (net, losses). X, T are scaled in place."""
     import torch
-    X /= torch.as_tensor(in_scale, device=X.device)[None, :, None, None]
-    T /= torch.as_tensor(out_scale, device=T.device)[None, :, None, None]
+    apply_scales(X, in_scale)
+    apply_scales(T, out_scale)
     if net is None:
         net = zk.Net()
         net.set_params(init_params(seed, net.nparam))

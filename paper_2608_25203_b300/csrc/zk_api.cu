@@ -71,6 +71,7 @@ struct zk_ctx {
     // learned closure (FP32): order-base_M right-hand side plus the network's residual
     zk_net* net = nullptr;
     bool closure_on = false;
+    bool closure_once = false;   // evaluate the network at the first RK stage only, reuse it after
     int base_M = 2;
     ClosureScales sc{};
     int check_every = 0;
@@ -529,7 +530,10 @@ struct Pipe {
 
     // One closure right-hand side at (se, sp): order-base_M right-hand side,
     // the residual, and the combination/epilogue of `fin` (mode set by the caller).
-    static cudaError_t closure_stage(zk_ctx* c, const cx<T>* se, const cx<T>* sp, ColArgs<T> fin, cudaStream_t s, int* nl) {
+    // With reuse, the residual spectrum of the previous evaluation (held in cspec) is applied
+    // again instead of evaluating the network at this state.
+    static cudaError_t closure_stage(zk_ctx* c, const cx<T>* se, const cx<T>* sp, ColArgs<T> fin, cudaStream_t s, int* nl,
+                                     bool reuse = false) {
         ColArgs<T> r = col_base(c);
         r.mode = FIN_RHS;
         r.ko_eta = C(c->ko_eta);
@@ -538,7 +542,7 @@ struct Pipe {
         c->m_run = c->base_M;
         cudaError_t e = rhs(c, se, sp, r, s, nl);
         c->m_run = save;
-        if (e == cudaSuccess) e = closure_residual(c, se, sp, s, nl);
+        if (e == cudaSuccess && !reuse) e = closure_residual(c, se, sp, s, nl);
         if (e == cudaSuccess) {
             const long long n = (long long)c->nz * c->hx;
             fin.ko_eta = C(c->ko_eta);
@@ -560,7 +564,7 @@ struct Pipe {
             fin.ka_eta = C(c->ka_eta); fin.ka_psi = C(c->ka_psi);
             const cx<T>* se = st == 1 ? C(c->y_eta) : C(c->ys_eta);
             const cx<T>* sp = st == 1 ? C(c->y_psi) : C(c->ys_psi);
-            cudaError_t e = closure_stage(c, se, sp, fin, s, nlaunch);
+            cudaError_t e = closure_stage(c, se, sp, fin, s, nlaunch, c->closure_once && st > 1);
             if (e != cudaSuccess) return e;
         }
         return cudaSuccess;
@@ -1631,6 +1635,15 @@ zk_status zk_closure_set(zk_ctx* c, zk_net* net, int base_order, const float* in
     c->fallback_step = -1;
     c->last_err = -1.0;
     drop_graph(c);
+    return ZK_OK;
+}
+
+zk_status zk_closure_set_once_per_step(zk_ctx* c, int on) {
+    if (!c || (on != 0 && on != 1)) return ZK_EINVAL;
+    if (c->closure_once != (on == 1)) {
+        c->closure_once = on == 1;
+        drop_graph(c);
+    }
     return ZK_OK;
 }
 

@@ -190,6 +190,48 @@ __global__ void mse_kernel(const float* __restrict__ y, const float* __restrict_
     }
 }
 
+// Data preparation of the closure's training set ([n][c][hw] FP32, channel-major per sample):
+// sums of squares per channel, block (channel ch, slice b) over elements i = b, b + nb, ... of
+// the channel's n*hw values, reduced in a fixed order (deterministic), FP64 accumulation.
+__global__ void __launch_bounds__(256) chan_sumsq_kernel(const float* __restrict__ x, long long n, int c, int hw,
+                                                         int nb, double* __restrict__ part) {
+    const int ch = blockIdx.y;
+    const long long per = n * hw;
+    double acc = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < per; i += (long long)nb * blockDim.x) {
+        const long long smp = i / hw, off = i - smp * hw;
+        const double v = x[(smp * c + ch) * hw + off];
+        acc += v * v;
+    }
+    __shared__ double red[8];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        part[(long long)ch * nb + blockIdx.x] = t;
+    }
+}
+
+// rms[ch] = sqrt(sum of the channel's partials / count), the partials taken in order.
+__global__ void chan_rms_kernel(const double* __restrict__ part, int c, int nb, double count, float* __restrict__ rms) {
+    const int ch = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ch >= c) return;
+    double t = 0.0;
+    for (int b = 0; b < nb; ++b) t += part[(long long)ch * nb + b];
+    rms[ch] = (float)sqrt(t / count);
+}
+
+// x[smp][ch][:] *= mul[ch] in place.
+__global__ void chan_scale_kernel(float* __restrict__ x, long long total, int c, int hw, const float* __restrict__ mul) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const int ch = (int)((i / hw) % c);
+        x[i] *= mul[ch];
+    }
+}
+
 __global__ void sum_kernel(const double* __restrict__ part, int n, double scale, double* __restrict__ out) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         double s = 0.0;
@@ -431,6 +473,45 @@ cudaError_t zk_net_infer(zk_net* n, const float* x, const float** y, int B, int 
 }
 
 extern "C" {
+
+zk_status zk_net_channel_rms(const float* x, long long n, int c, int hw, float* rms, void* stream) {
+    if (!x || !rms || n <= 0 || c <= 0 || c > 64 || hw <= 0) return ZK_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    constexpr int kSlices = 256;
+    double* part = nullptr;
+    float* drms = nullptr;
+    if (cudaMallocAsync((void**)&part, sizeof(double) * kSlices * c, s) != cudaSuccess) { cudaGetLastError(); return ZK_ENOMEM; }
+    if (cudaMallocAsync((void**)&drms, sizeof(float) * c, s) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFreeAsync(part, s);
+        return ZK_ENOMEM;
+    }
+    chan_sumsq_kernel<<<dim3(kSlices, c), 256, 0, s>>>(x, n, c, hw, kSlices, part);
+    chan_rms_kernel<<<1, 64, 0, s>>>(part, c, kSlices, (double)n * hw, drms);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(rms, drms, sizeof(float) * c, cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(part, s);
+    cudaFreeAsync(drms, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e == cudaSuccess ? ZK_OK : ZK_ECUDA;
+}
+
+zk_status zk_net_scale_channels(float* x, long long n, int c, int hw, const float* mul, void* stream) {
+    if (!x || !mul || n <= 0 || c <= 0 || c > 64 || hw <= 0) return ZK_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    float* dmul = nullptr;
+    if (cudaMallocAsync((void**)&dmul, sizeof(float) * c, s) != cudaSuccess) { cudaGetLastError(); return ZK_ENOMEM; }
+    cudaError_t e = cudaMemcpyAsync(dmul, mul, sizeof(float) * c, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        const long long total = n * c * (long long)hw;
+        const int blocks = (int)std::min<long long>((total + 255) / 256, 148LL * 32);
+        chan_scale_kernel<<<blocks, 256, 0, s>>>(x, total, c, hw, dmul);
+        e = cudaGetLastError();
+    }
+    cudaFreeAsync(dmul, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e == cudaSuccess ? ZK_OK : ZK_ECUDA;
+}
 
 void zk_net_destroy(zk_net* n) {
     if (!n) return;

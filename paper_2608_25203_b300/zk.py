@@ -37,8 +37,9 @@ EXPORTS = [
     "zk_batch_autotune",
     "zk_net_create", "zk_net_destroy", "zk_net_param_count", "zk_net_set_params", "zk_net_get_params",
     "zk_net_forward", "zk_net_backward", "zk_net_adam", "zk_net_train_step", "zk_net_set_inference",
+    "zk_net_channel_rms", "zk_net_scale_channels",
     "zk_net_predict",
-    "zk_closure_features", "zk_closure_set", "zk_closure_status",
+    "zk_closure_features", "zk_closure_set", "zk_closure_set_once_per_step", "zk_closure_status",
     "zk_strerror", "zk_version",
 ]
 
@@ -125,10 +126,13 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "zk_net_backward": ([vp, vp, vp, vp, vp], i),
         "zk_net_adam": ([vp, vp, d, vp], i),
         "zk_net_train_step": ([vp, vp, vp, i, i, i, d, pd, vp], i),
+        "zk_net_channel_rms": ([vp, ctypes.c_longlong, i, i, vp, vp], i),
+        "zk_net_scale_channels": ([vp, ctypes.c_longlong, i, i, vp, vp], i),
         "zk_net_set_inference": ([vp, i], i),
         "zk_net_predict": ([vp, vp, vp, i, i, vp], i),
         "zk_closure_features": ([vp, i, vp, vp, vp, vp], i),
         "zk_closure_set": ([vp, vp, i, vp, vp, i, d], i),
+        "zk_closure_set_once_per_step": ([vp, i], i),
         "zk_closure_status": ([vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(ctypes.c_longlong), pd], i),
         "zk_strerror": ([i], ctypes.c_char_p),
         "zk_version": ([], ctypes.c_char_p),
@@ -637,6 +641,25 @@ def zk_net_train_step(n, x, target, lr, stream=None, want_loss=True):
     return loss.value
 
 
+def zk_net_channel_rms(x, stream=None):
+    """Per-channel RMS over samples and positions of a [n][c][h][w] float32 CUDA tensor (numpy float32 [c])."""
+    n, c = x.shape[0], x.shape[1]
+    hw = int(np.prod(x.shape[2:]))
+    out = np.empty(c, np.float32)
+    _check("zk_net_channel_rms", load().zk_net_channel_rms(_dptr(x), int(n), int(c), hw, out.ctypes.data, stream))
+    return out
+
+
+def zk_net_scale_channels(x, mul, stream=None):
+    """x[:, ch] *= mul[ch] in place on a [n][c][h][w] float32 CUDA tensor."""
+    n, c = x.shape[0], x.shape[1]
+    hw = int(np.prod(x.shape[2:]))
+    m = np.ascontiguousarray(mul, dtype=np.float32)
+    if m.shape != (c,):
+        raise ValueError("one factor per channel expected")
+    _check("zk_net_scale_channels", load().zk_net_scale_channels(_dptr(x), int(n), int(c), hw, m.ctypes.data, stream))
+
+
 def zk_net_set_inference(n, mode):
     _check("zk_net_set_inference", load().zk_net_set_inference(n, int(mode)))
 
@@ -658,6 +681,10 @@ def zk_closure_set(ctx, net, base_order=2, in_scale=None, out_scale=None, check_
     _check("zk_closure_set", load().zk_closure_set(
         ctx, net, int(base_order), None if a is None else a.ctypes.data, None if b is None else b.ctypes.data,
         int(check_every), float(check_tol)))
+
+
+def zk_closure_set_once_per_step(ctx, on):
+    _check("zk_closure_set_once_per_step", load().zk_closure_set_once_per_step(ctx, int(on)))
 
 
 def zk_closure_status(ctx):

@@ -91,6 +91,34 @@ def test_closure_rhs_and_steps(zk, sea):
     assert st["active"] == 1 and st["checks"] == 0
 
 
+def test_closure_once_per_step(zk, sea):
+    # the network at the first RK stage only, its residual reused by stages 2-4: against the
+    # oracle's RK4 with the residual frozen at each step's start state, same bar as above
+    gr, o2, o6 = _oracles()
+    theta = _theta(7)
+    net = zk.Net(theta)
+    s = zk.Zakharov(N, N, L, L, H, M=6, eps=EPS)
+    s.set_state(*sea)
+    zk.zk_closure_set(s.ctx, net.n, 2, IN, OUT, check_every=0)
+    zk.zk_closure_set_once_per_step(s.ctx, 1)
+    co = cl.ClosureOracle(gr, 2, theta.astype(np.float64), IN, OUT, eps=EPS)
+    eh, ph = co.spectrum(sea[0].astype(np.float64)), co.spectrum(sea[1].astype(np.float64))
+    n = 5
+    s.step(0.02, n)
+    for _ in range(n):
+        eh, ph = co.step_rk4_frozen(eh, ph, 0.02)
+    ge, gp = s.get_state()
+    assert rel(ge, co.physical(eh)) < 4 * n * 2.0 ** -24 + 1e-6
+    assert rel(gp, co.physical(ph)) < 4 * n * 2.0 ** -24 + 1e-6
+    # and it is not the per-stage closure (the frozen residual changes the step)
+    e2, p2 = co.spectrum(sea[0].astype(np.float64)), co.spectrum(sea[1].astype(np.float64))
+    for _ in range(n):
+        e2, p2 = co.step_rk4(e2, p2, 0.02)
+    assert rel(co.physical(eh), co.physical(e2)) > 0
+    with pytest.raises(zk.ZkError):
+        zk.zk_closure_set_once_per_step(s.ctx, 2)
+
+
 def test_zero_net_is_base_order(zk, sea):
     net = zk.Net(np.zeros(cl.param_count(), np.float32))
     s = zk.Zakharov(N, N, L, L, H, M=6, eps=EPS)

@@ -136,3 +136,27 @@ def test_closure_with_zero_net_is_base_rhs():
     d0, d1 = a[0] - b[0], a[1] - b[1]
     assert np.abs(d0).max() < 1e-12
     assert abs(d1[0, 0] - (-0.5) * 16 * 16) < 1e-9 and np.abs(d1.ravel()[1:]).max() < 1e-9
+
+
+def test_frozen_residual_step():
+    """RK4 with the residual evaluated once per step (at the start state):
+    * a residual that does not depend on the state (output bias only) gives the per-stage step;
+    * otherwise the two steps differ by O(dt^2): the stage states move O(dt) from the start,
+      and dt times an O(dt) change of the residual enters the step. Halving dt quarters it."""
+    gr = Grid(16, 16, 20.0, 20.0, 5.0)
+    o2 = Oracle(gr, 2, eps=0.5)
+    rng = np.random.default_rng(8)
+    eh = o2.spectrum(rng.standard_normal((16, 16)) * 0.05)
+    ph = o2.spectrum(rng.standard_normal((16, 16)) * 0.1)
+    theta = np.zeros(cl.param_count())
+    theta[-2:] = [0.25, -0.5]
+    co = cl.ClosureOracle(gr, 2, theta, np.ones(6), np.ones(2), eps=0.5)
+    a, b = co.step_rk4_frozen(eh, ph, 0.05), co.step_rk4(eh, ph, 0.05)
+    assert np.abs(a[0] - b[0]).max() < 1e-13 and np.abs(a[1] - b[1]).max() < 1e-13
+    theta = cl.init_params(3) + 0.05 * rng.standard_normal(cl.param_count())
+    co = cl.ClosureOracle(gr, 2, theta, np.full(6, 0.2), np.full(2, 0.05), eps=0.5)
+    d = []
+    for dt in (0.04, 0.02):
+        a, b = co.step_rk4_frozen(eh, ph, dt), co.step_rk4(eh, ph, dt)
+        d.append(np.linalg.norm(a[0] - b[0]) + np.linalg.norm(a[1] - b[1]))
+    assert d[0] > 0 and 3.5 < d[0] / d[1] < 4.5, d
