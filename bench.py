@@ -405,7 +405,9 @@ def closure_arm(args):
     nv = 40
     Xv, Tv = X[-nv:].clone(), T[-nv:].clone()
     t0 = time.time()
-    net, losses = ct.train(X[:-nv], T[:-nv], ins, outs, iters=3000, batch=8, lr=1e-3, lr_end=1e-5, log_every=500)
+    # 12000 Adam steps: the held-out error then stays under the fallback check's tolerance on the
+    # evaluation seas (3000 steps left the check at 0.225 against the tolerance of 0.2)
+    net, losses = ct.train(X[:-nv], T[:-nv], ins, outs, iters=12000, batch=8, lr=1e-3, lr_end=1e-5, log_every=2000)
     torch.cuda.synchronize()
     t_train = time.time() - t0
     ct.apply_scales(Xv, ins)
@@ -485,7 +487,7 @@ def closure_arm(args):
         "config": {"workload": "closure M=2 + 4-layer conv net (6-32-32-32-2) vs plain M=2..6; eval JONSWAP "
                                "Hs=3 Tp=10 h=30, eps=0.5, RK4 dt=0.02, seeds 7, 8; train 512^2 seeds 100-163"},
         "training": {"pairs": int(20 * len(kept)), "trajectories": len(kept), "data_s": t_data, "train_s": t_train,
-                     "iters": 3000, "batch": 8, "val_loss_scaled": val, "losses": losses,
+                     "iters": 12000, "batch": 8, "val_loss_scaled": val, "losses": losses,
                      "in_scale": [float(x) for x in ins], "out_scale": [float(x) for x in outs]},
         "results": results}), flush=True)
     net.close()
