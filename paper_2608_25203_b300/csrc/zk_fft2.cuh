@@ -45,6 +45,25 @@ __device__ __forceinline__ int stage_slot(int pb, int base, int m) {
     else return pidx(base + m * SUB);
 }
 
+// Thread order of the radix-8 stages whose sub-blocks are narrower than 16 (SUB = 2, 4, 8):
+// in the natural order the 16/SUB blocks a half-warp touches start at block offsets
+// blk * B/16 (mod 16 slots) that overlap, a 2-way bank conflict on every 64-bit access.
+// Moving lane bit 4 below the block bits hands each half-warp every other block, whose
+// offsets are SUB slots apart, so its 16 accesses cover all 32 banks. The permutation
+// stays inside each warp and keeps n1 = lane mod SUB (the fixed twiddles).
+template <int B, int R, int SUB>
+__host__ __device__ constexpr bool stage_swizzled() {
+    return R == 8 && SUB >= 2 && SUB < 16 && 16 % SUB == 0 && B % 16 == 0;
+}
+template <int SUB>
+__device__ __forceinline__ int swz_lane(int t) {
+    constexpr int LS = SUB == 2 ? 1 : SUB == 4 ? 2 : 3;   // log2 SUB
+    constexpr int LH = 4 - LS;                            // log2 of the blocks per half-warp
+    const int lo = t & 31, j = lo >> LS;
+    const int jn = ((j & ((1 << LH) - 1)) << 1) | (j >> LH);
+    return (t & ~31) | (jn << LS) | (lo & (SUB - 1));
+}
+
 // Twiddles: one table per plan holding, stage after stage, w_B^{n1 m} at
 // [(m-1) * SUB + n1] (m = 1..R-1, n1 < SUB), so a warp's loads for one m are
 // contiguous. OFF is the stage's offset in that table.
@@ -60,9 +79,10 @@ __device__ __forceinline__ void dif_stage(cx<T>* buf, const cx<T>* __restrict__ 
 #pragma unroll
         for (int m = 1; m < R; ++m) wf[m - 1] = __ldg(&tws[OFF + (m - 1) * SUB + lt % SUB]);
     }
+    const int lts = (stage_swizzled<B, R, SUB>() && TL % 32 == 0) ? swz_lane<SUB>(lt) : lt;
 #pragma unroll
     for (int p = 0; p < NB / TL; ++p) {
-        const int b = lt + p * TL;
+        const int b = lts + p * TL;
         const int blk = b / SUB, n1 = b - blk * SUB;
         const int base = blk * B + n1;
         const int pb = stage_pbase<B, SUB>(blk, n1);
@@ -92,9 +112,10 @@ __device__ __forceinline__ void dit_stage(cx<T>* buf, const cx<T>* __restrict__ 
 #pragma unroll
         for (int m = 1; m < R; ++m) wf[m - 1] = __ldg(&tws[OFF + (m - 1) * SUB + lt % SUB]);
     }
+    const int lts = (stage_swizzled<B, R, SUB>() && TL % 32 == 0) ? swz_lane<SUB>(lt) : lt;
 #pragma unroll
     for (int p = 0; p < NB / TL; ++p) {
-        const int b = lt + p * TL;
+        const int b = lts + p * TL;
         const int blk = b / SUB, n1 = b - blk * SUB;
         const int base = blk * B + n1;
         const int pb = stage_pbase<B, SUB>(blk, n1);
@@ -174,7 +195,8 @@ __device__ __forceinline__ void dit_run(cx<T>* buf, const cx<T>* __restrict__ tw
 template <int N, int B, int R, bool INV, typename T, int OFF>
 __device__ __forceinline__ void dit_stage_blk(cx<T>* buf, const cx<T>* __restrict__ tws, int tid, int nt) {
     constexpr int SUB = B / R, NB = N / R;
-    for (int b = tid; b < NB; b += nt) {
+    const int tds = (stage_swizzled<B, R, SUB>() && NB % 32 == 0 && nt % 32 == 0) ? swz_lane<SUB>(tid) : tid;
+    for (int b = tds; b < NB; b += nt) {
         const int blk = b / SUB, n1 = b - blk * SUB;
         const int base = blk * B + n1;
         const int pb = stage_pbase<B, SUB>(blk, n1);
@@ -237,9 +259,10 @@ __device__ __forceinline__ void dit_stage_w(cx<T>* buf, const cx<T>* __restrict_
 #pragma unroll
         for (int m = 1; m < R; ++m) wf[m - 1] = __ldg(&tws[OFF + (m - 1) * SUB + tid % SUB]);
     }
+    const int tds = (stage_swizzled<B, R, SUB>() && TLB % 32 == 0 && NB % 32 == 0) ? swz_lane<SUB>(tid) : tid;
 #pragma unroll
     for (int p = 0; p < PER; ++p) {
-        const int b = tid + p * TLB;
+        const int b = tds + p * TLB;
         if (EVEN || b < NB) {
             const int blk = b / SUB, n1 = b - blk * SUB;
             const int base = blk * B + n1;
@@ -336,7 +359,7 @@ ZK_IPLAN(96, 0, 2, 6, 16)
 ZK_IPLAN(192, 0, 4, 12, 16)
 ZK_IPLAN(384, 0, 8, 6, 4, 16)
 // radix-8 plans: every stage has N/R divisible by 128 (3072), 64 (1536) or
-// 32 (768); one 2-way bank conflict remains in the third stage
+// 32 (768); the third stage (SUB = 8) runs in the swizzled thread order above
 ZK_IPLAN(768, 0, 32, 3, 4, 8, 8)
 ZK_IPLAN(1536, 0, 64, 3, 8, 8, 8)
 ZK_IPLAN(3072, 0, 128, 6, 8, 8, 8)
