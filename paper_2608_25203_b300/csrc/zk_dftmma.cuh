@@ -176,7 +176,7 @@ struct IPlanSplit {
         static_assert(sizeof(T) == 4, "split-precision stages are FP32 only");
         dif_first<N, R1, TL, INV, T>(b, tws, lt, ld);
         group_sync<TL>(bar);
-        dif_run<N, N / R1, TL, INV, T, OFF, 8, 8>(b, tws, lt, bar);
+        dif_run<N, N / R1, TL, INV, T, OFF, false, 8, 8>(b, tws, lt, bar);
         dft8_line<N, TL, INV, PREC>(b, lt);
         group_sync<TL>(bar);
     }
@@ -185,7 +185,7 @@ struct IPlanSplit {
         static_assert(sizeof(T) == 4, "split-precision stages are FP32 only");
         dft8_line<N, TL, INV, PREC>(b, lt);
         group_sync<TL>(bar);
-        dit_run<N, N / R1, TL, INV, T, OFF, 8, 8>(b, tws, lt, bar);
+        dit_run<N, N / R1, TL, INV, T, OFF, false, 8, 8>(b, tws, lt, bar);
         dit_last<N, R1, TL, INV, T>(b, tws, lt, st);
     }
     template <bool INV, typename T, class Store>
@@ -194,7 +194,7 @@ struct IPlanSplit {
         static_assert(sizeof(T) == 4, "split-precision stages are FP32 only");
         dft8_line_blk<N, INV, PREC>(b, tid, nt);
         __syncthreads();
-        dit_run_blk<N, N / R1, INV, T, OFF, 8, 8>(b, tws, tid, nt);
+        dit_run_blk<N, N / R1, INV, T, OFF, false, 8, 8>(b, tws, tid, nt);
         dit_last_blk<N, R1, INV, T>(b, tws, tid, nt, st);
     }
     template <int TLB, bool INV, typename T, class Store>
@@ -203,7 +203,7 @@ struct IPlanSplit {
         static_assert(sizeof(T) == 4, "split-precision stages are FP32 only");
         dft8_line_blk<N, INV, PREC>(b, tid, TLB);
         wide_sync<TLB>(bar);
-        dit_run_w<N, N / R1, TLB, INV, T, OFF, 8, 8>(b, tws, tid, bar);
+        dit_run_w<N, N / R1, TLB, INV, T, OFF, false, 8, 8>(b, tws, tid, bar);
         dit_last_w<N, R1, TLB, INV, T>(b, tws, tid, st);
     }
 };

@@ -50,7 +50,9 @@ __device__ __forceinline__ int stage_slot(int pb, int base, int m) {
 // blk * B/16 (mod 16 slots) that overlap, a 2-way bank conflict on every 64-bit access.
 // Moving lane bit 4 below the block bits hands each half-warp every other block, whose
 // offsets are SUB slots apart, so its 16 accesses cover all 32 banks. The permutation
-// stays inside each warp and keeps n1 = lane mod SUB (the fixed twiddles).
+// stays inside each warp and keeps n1 = lane mod SUB (the fixed twiddles). The stage
+// runners' SWZ switch keeps the natural order instead (the split-precision plans: with the
+// swizzle ptxas gave their 1536-point row kernels 100 registers instead of 64).
 template <int B, int R, int SUB>
 __host__ __device__ constexpr bool stage_swizzled() {
     return R == 8 && SUB >= 2 && SUB < 16 && 16 % SUB == 0 && B % 16 == 0;
@@ -67,7 +69,7 @@ __device__ __forceinline__ int swz_lane(int t) {
 // Twiddles: one table per plan holding, stage after stage, w_B^{n1 m} at
 // [(m-1) * SUB + n1] (m = 1..R-1, n1 < SUB), so a warp's loads for one m are
 // contiguous. OFF is the stage's offset in that table.
-template <int N, int B, int R, int TL, bool INV, typename T, int OFF>
+template <int N, int B, int R, int TL, bool INV, typename T, int OFF, bool SWZ = true>
 __device__ __forceinline__ void dif_stage(cx<T>* buf, const cx<T>* __restrict__ tws, int lt) {
     constexpr int SUB = B / R, NB = N / R;
     static_assert(NB % TL == 0, "line group width must divide N/R");
@@ -79,7 +81,7 @@ __device__ __forceinline__ void dif_stage(cx<T>* buf, const cx<T>* __restrict__ 
 #pragma unroll
         for (int m = 1; m < R; ++m) wf[m - 1] = __ldg(&tws[OFF + (m - 1) * SUB + lt % SUB]);
     }
-    const int lts = (stage_swizzled<B, R, SUB>() && TL % 32 == 0) ? swz_lane<SUB>(lt) : lt;
+    const int lts = (SWZ && stage_swizzled<B, R, SUB>() && TL % 32 == 0) ? swz_lane<SUB>(lt) : lt;
 #pragma unroll
     for (int p = 0; p < NB / TL; ++p) {
         const int b = lts + p * TL;
@@ -100,7 +102,7 @@ __device__ __forceinline__ void dif_stage(cx<T>* buf, const cx<T>* __restrict__ 
     }
 }
 
-template <int N, int B, int R, int TL, bool INV, typename T, int OFF>
+template <int N, int B, int R, int TL, bool INV, typename T, int OFF, bool SWZ = true>
 __device__ __forceinline__ void dit_stage(cx<T>* buf, const cx<T>* __restrict__ tws, int lt) {
     constexpr int SUB = B / R, NB = N / R;
     static_assert(NB % TL == 0, "line group width must divide N/R");
@@ -112,7 +114,7 @@ __device__ __forceinline__ void dit_stage(cx<T>* buf, const cx<T>* __restrict__ 
 #pragma unroll
         for (int m = 1; m < R; ++m) wf[m - 1] = __ldg(&tws[OFF + (m - 1) * SUB + lt % SUB]);
     }
-    const int lts = (stage_swizzled<B, R, SUB>() && TL % 32 == 0) ? swz_lane<SUB>(lt) : lt;
+    const int lts = (SWZ && stage_swizzled<B, R, SUB>() && TL % 32 == 0) ? swz_lane<SUB>(lt) : lt;
 #pragma unroll
     for (int p = 0; p < NB / TL; ++p) {
         const int b = lts + p * TL;
@@ -173,29 +175,29 @@ __device__ __forceinline__ void dit_last(const cx<T>* buf, const cx<T>* __restri
     }
 }
 
-template <int N, int B, int TL, bool INV, typename T, int OFF, int R, int... Rest>
+template <int N, int B, int TL, bool INV, typename T, int OFF, bool SWZ, int R, int... Rest>
 __device__ __forceinline__ void dif_run(cx<T>* buf, const cx<T>* __restrict__ tws, int lt, int bar) {
-    dif_stage<N, B, R, TL, INV, T, OFF>(buf, tws, lt);
+    dif_stage<N, B, R, TL, INV, T, OFF, SWZ>(buf, tws, lt);
     group_sync<TL>(bar);
     if constexpr (sizeof...(Rest) > 0)
-        dif_run<N, B / R, TL, INV, T, OFF + (R - 1) * (B / R), Rest...>(buf, tws, lt, bar);
+        dif_run<N, B / R, TL, INV, T, OFF + (R - 1) * (B / R), SWZ, Rest...>(buf, tws, lt, bar);
 }
 
-template <int N, int B, int TL, bool INV, typename T, int OFF, int R, int... Rest>
+template <int N, int B, int TL, bool INV, typename T, int OFF, bool SWZ, int R, int... Rest>
 __device__ __forceinline__ void dit_run(cx<T>* buf, const cx<T>* __restrict__ tws, int lt, int bar) {
     if constexpr (sizeof...(Rest) > 0)
-        dit_run<N, B / R, TL, INV, T, OFF + (R - 1) * (B / R), Rest...>(buf, tws, lt, bar);
-    dit_stage<N, B, R, TL, INV, T, OFF>(buf, tws, lt);
+        dit_run<N, B / R, TL, INV, T, OFF + (R - 1) * (B / R), SWZ, Rest...>(buf, tws, lt, bar);
+    dit_stage<N, B, R, TL, INV, T, OFF, SWZ>(buf, tws, lt);
     group_sync<TL>(bar);
 }
 
 // ---- whole-block variants: every thread of the block works on one line ----
 // (nt = blockDim.x threads, __syncthreads between stages). Used where one
 // line must be transformed while the rest of the block would otherwise idle.
-template <int N, int B, int R, bool INV, typename T, int OFF>
+template <int N, int B, int R, bool INV, typename T, int OFF, bool SWZ = true>
 __device__ __forceinline__ void dit_stage_blk(cx<T>* buf, const cx<T>* __restrict__ tws, int tid, int nt) {
     constexpr int SUB = B / R, NB = N / R;
-    const int tds = (stage_swizzled<B, R, SUB>() && NB % 32 == 0 && nt % 32 == 0) ? swz_lane<SUB>(tid) : tid;
+    const int tds = (SWZ && stage_swizzled<B, R, SUB>() && NB % 32 == 0 && nt % 32 == 0) ? swz_lane<SUB>(tid) : tid;
     for (int b = tds; b < NB; b += nt) {
         const int blk = b / SUB, n1 = b - blk * SUB;
         const int base = blk * B + n1;
@@ -213,11 +215,11 @@ __device__ __forceinline__ void dit_stage_blk(cx<T>* buf, const cx<T>* __restric
     }
 }
 
-template <int N, int B, bool INV, typename T, int OFF, int R, int... Rest>
+template <int N, int B, bool INV, typename T, int OFF, bool SWZ, int R, int... Rest>
 __device__ __forceinline__ void dit_run_blk(cx<T>* buf, const cx<T>* __restrict__ tws, int tid, int nt) {
     if constexpr (sizeof...(Rest) > 0)
-        dit_run_blk<N, B / R, INV, T, OFF + (R - 1) * (B / R), Rest...>(buf, tws, tid, nt);
-    dit_stage_blk<N, B, R, INV, T, OFF>(buf, tws, tid, nt);
+        dit_run_blk<N, B / R, INV, T, OFF + (R - 1) * (B / R), SWZ, Rest...>(buf, tws, tid, nt);
+    dit_stage_blk<N, B, R, INV, T, OFF, SWZ>(buf, tws, tid, nt);
     __syncthreads();
 }
 
@@ -248,7 +250,12 @@ __device__ __forceinline__ void wide_sync(int bar) {
     else asm volatile("bar.sync %0, %1;" ::"r"(bar), "n"(TLB) : "memory");
 }
 
-template <int N, int B, int R, int TLB, bool INV, typename T, int OFF>
+// SWZ: the swizzled order of the 8-wide radix-8 stage, taken only where the line does not
+// divide evenly among the group's threads. Elsewhere in the wide stages, and in every wide
+// stage of the split-precision plans, it raised ptxas's register count of the whole row kernel
+// (1536-point rows: 64 -> 100 registers, a third fewer blocks per SM), which cost more than the
+// bank conflict.
+template <int N, int B, int R, int TLB, bool INV, typename T, int OFF, bool SWZ = true>
 __device__ __forceinline__ void dit_stage_w(cx<T>* buf, const cx<T>* __restrict__ tws, int tid) {
     constexpr int SUB = B / R, NB = N / R;
     constexpr int PER = (NB + TLB - 1) / TLB;
@@ -259,7 +266,7 @@ __device__ __forceinline__ void dit_stage_w(cx<T>* buf, const cx<T>* __restrict_
 #pragma unroll
         for (int m = 1; m < R; ++m) wf[m - 1] = __ldg(&tws[OFF + (m - 1) * SUB + tid % SUB]);
     }
-    const int tds = (stage_swizzled<B, R, SUB>() && TLB % 32 == 0 && NB % 32 == 0) ? swz_lane<SUB>(tid) : tid;
+    const int tds = (SWZ && stage_swizzled<B, R, SUB>() && !EVEN && TLB % 32 == 0 && NB % 32 == 0) ? swz_lane<SUB>(tid) : tid;
 #pragma unroll
     for (int p = 0; p < PER; ++p) {
         const int b = tds + p * TLB;
@@ -282,11 +289,11 @@ __device__ __forceinline__ void dit_stage_w(cx<T>* buf, const cx<T>* __restrict_
     }
 }
 
-template <int N, int B, int TLB, bool INV, typename T, int OFF, int R, int... Rest>
+template <int N, int B, int TLB, bool INV, typename T, int OFF, bool SWZ, int R, int... Rest>
 __device__ __forceinline__ void dit_run_w(cx<T>* buf, const cx<T>* __restrict__ tws, int tid, int bar) {
     if constexpr (sizeof...(Rest) > 0)
-        dit_run_w<N, B / R, TLB, INV, T, OFF + (R - 1) * (B / R), Rest...>(buf, tws, tid, bar);
-    dit_stage_w<N, B, R, TLB, INV, T, OFF>(buf, tws, tid);
+        dit_run_w<N, B / R, TLB, INV, T, OFF + (R - 1) * (B / R), SWZ, Rest...>(buf, tws, tid, bar);
+    dit_stage_w<N, B, R, TLB, INV, T, OFF, SWZ>(buf, tws, tid);
     wide_sync<TLB>(bar);
 }
 
@@ -332,24 +339,24 @@ template <int N, int V = 0> struct IPlan;
                                                    int bar, Load ld) {                                   \
             dif_first<N_, R1_, TL_, INV, T>(b, tws, lt, ld);                                             \
             group_sync<TL_>(bar);                                                                        \
-            dif_run<N_, N_ / R1_, TL_, INV, T, (R1_ - 1) * (N_ / R1_), __VA_ARGS__>(b, tws, lt, bar);    \
+            dif_run<N_, N_ / R1_, TL_, INV, T, (R1_ - 1) * (N_ / R1_), true, __VA_ARGS__>(b, tws, lt, bar); \
         }                                                                                                \
         template <bool INV, typename T, class Store>                                                     \
         static __device__ __forceinline__ void dit(cx<T>* b, const cx<T>* __restrict__ tws, int lt,      \
                                                    int bar, Store st) {                                  \
-            dit_run<N_, N_ / R1_, TL_, INV, T, (R1_ - 1) * (N_ / R1_), __VA_ARGS__>(b, tws, lt, bar);    \
+            dit_run<N_, N_ / R1_, TL_, INV, T, (R1_ - 1) * (N_ / R1_), true, __VA_ARGS__>(b, tws, lt, bar); \
             dit_last<N_, R1_, TL_, INV, T>(b, tws, lt, st);                                              \
         }                                                                                                \
         template <bool INV, typename T, class Store>                                                     \
         static __device__ __forceinline__ void dit_blk(cx<T>* b, const cx<T>* __restrict__ tws, int tid, \
                                                        int nt, Store st) {                               \
-            dit_run_blk<N_, N_ / R1_, INV, T, (R1_ - 1) * (N_ / R1_), __VA_ARGS__>(b, tws, tid, nt);     \
+            dit_run_blk<N_, N_ / R1_, INV, T, (R1_ - 1) * (N_ / R1_), true, __VA_ARGS__>(b, tws, tid, nt); \
             dit_last_blk<N_, R1_, INV, T>(b, tws, tid, nt, st);                                          \
         }                                                                                                \
         template <int TLB, bool INV, typename T, class Store>                                            \
         static __device__ __forceinline__ void dit_wide(cx<T>* b, const cx<T>* __restrict__ tws, int tid,\
                                                         int bar, Store st) {                             \
-            dit_run_w<N_, N_ / R1_, TLB, INV, T, (R1_ - 1) * (N_ / R1_), __VA_ARGS__>(b, tws, tid, bar); \
+            dit_run_w<N_, N_ / R1_, TLB, INV, T, (R1_ - 1) * (N_ / R1_), true, __VA_ARGS__>(b, tws, tid, bar); \
             dit_last_w<N_, R1_, TLB, INV, T>(b, tws, tid, st);                                           \
         }                                                                                                \
     };
