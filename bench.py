@@ -130,8 +130,8 @@ def peaks():
 # DRAM bytes per launch of each kernel class (dram__bytes_read.sum + dram__bytes_write.sum),
 # copied from one ncu capture of the current kernels; empty whenever the kernels have changed
 # since that capture, which makes the roofline's `traffic` null. TRAFFIC_SOURCE names it.
-TRAFFIC_NCU = {"col_state": 206.18e6, "row_round": 213.25e6, "col_phi": 43.65e6, "row_final": 397.31e6,
-               "col_final": 94.46e6}
+TRAFFIC_NCU = {"col_state": 206.33e6, "row_round": 213.20e6, "col_phi": 43.85e6, "row_final": 397.03e6,
+               "col_final": 94.60e6}
 TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, first right-hand side of the 2048^2 "
                   "M=5 workload (row kernel --set full -c 5, column kernel --set full -c 6, final-pass update "
                   "kernel -c 4), mean per class; profiles/traffic_2048_M5.md")
