@@ -161,6 +161,11 @@ __device__ __forceinline__ void dft8_line_blk(float2* line, int tid, int nt) {
     for (int grp = tid >> 5; grp < N / 64; grp += nt >> 5) dft8_group<INV, PREC>(line, grp, lane, F);
 }
 
+// The swizzled thread order of the 8-wide radix-8 stage (zk_fft2.cuh) in these plans: taken
+// for 3072-point lines; at 1536 points it raised ptxas's register count of the row kernel
+// from 64 to 100, which cost more than the bank conflict it removes.
+template <int N> constexpr bool kSplitSwz = N >= 3072;
+
 // Plans with the DFT-GEMM stage: the radices (R1, 8, 8, 8), line-group width
 // and twiddle table of the default (V = 0) plan of the same length; only the
 // block-8 stage is replaced.
@@ -176,7 +181,7 @@ struct IPlanSplit {
         static_assert(sizeof(T) == 4, "split-precision stages are FP32 only");
         dif_first<N, R1, TL, INV, T>(b, tws, lt, ld);
         group_sync<TL>(bar);
-        dif_run<N, N / R1, TL, INV, T, OFF, false, 8, 8>(b, tws, lt, bar);
+        dif_run<N, N / R1, TL, INV, T, OFF, kSplitSwz<N>, 8, 8>(b, tws, lt, bar);
         dft8_line<N, TL, INV, PREC>(b, lt);
         group_sync<TL>(bar);
     }
@@ -185,7 +190,7 @@ struct IPlanSplit {
         static_assert(sizeof(T) == 4, "split-precision stages are FP32 only");
         dft8_line<N, TL, INV, PREC>(b, lt);
         group_sync<TL>(bar);
-        dit_run<N, N / R1, TL, INV, T, OFF, false, 8, 8>(b, tws, lt, bar);
+        dit_run<N, N / R1, TL, INV, T, OFF, kSplitSwz<N>, 8, 8>(b, tws, lt, bar);
         dit_last<N, R1, TL, INV, T>(b, tws, lt, st);
     }
     template <bool INV, typename T, class Store>
@@ -194,7 +199,7 @@ struct IPlanSplit {
         static_assert(sizeof(T) == 4, "split-precision stages are FP32 only");
         dft8_line_blk<N, INV, PREC>(b, tid, nt);
         __syncthreads();
-        dit_run_blk<N, N / R1, INV, T, OFF, false, 8, 8>(b, tws, tid, nt);
+        dit_run_blk<N, N / R1, INV, T, OFF, kSplitSwz<N>, 8, 8>(b, tws, tid, nt);
         dit_last_blk<N, R1, INV, T>(b, tws, tid, nt, st);
     }
     template <int TLB, bool INV, typename T, class Store>
@@ -203,7 +208,7 @@ struct IPlanSplit {
         static_assert(sizeof(T) == 4, "split-precision stages are FP32 only");
         dft8_line_blk<N, INV, PREC>(b, tid, TLB);
         wide_sync<TLB>(bar);
-        dit_run_w<N, N / R1, TLB, INV, T, OFF, false, 8, 8>(b, tws, tid, bar);
+        dit_run_w<N, N / R1, TLB, INV, T, OFF, kSplitSwz<N>, 8, 8>(b, tws, tid, bar);
         dit_last_w<N, R1, TLB, INV, T>(b, tws, tid, st);
     }
 };

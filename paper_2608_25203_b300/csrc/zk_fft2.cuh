@@ -51,8 +51,8 @@ __device__ __forceinline__ int stage_slot(int pb, int base, int m) {
 // Moving lane bit 4 below the block bits hands each half-warp every other block, whose
 // offsets are SUB slots apart, so its 16 accesses cover all 32 banks. The permutation
 // stays inside each warp and keeps n1 = lane mod SUB (the fixed twiddles). The stage
-// runners' SWZ switch keeps the natural order instead (the split-precision plans: with the
-// swizzle ptxas gave their 1536-point row kernels 100 registers instead of 64).
+// runners' SWZ switch keeps the natural order instead (the split-precision plans below 3072
+// points: with the swizzle ptxas gave their 1536-point row kernels 100 registers, not 64).
 template <int B, int R, int SUB>
 __host__ __device__ constexpr bool stage_swizzled() {
     return R == 8 && SUB >= 2 && SUB < 16 && 16 % SUB == 0 && B % 16 == 0;
@@ -251,10 +251,10 @@ __device__ __forceinline__ void wide_sync(int bar) {
 }
 
 // SWZ: the swizzled order of the 8-wide radix-8 stage, taken only where the line does not
-// divide evenly among the group's threads. Elsewhere in the wide stages, and in every wide
-// stage of the split-precision plans, it raised ptxas's register count of the whole row kernel
-// (1536-point rows: 64 -> 100 registers, a third fewer blocks per SM), which cost more than the
-// bank conflict.
+// divide evenly among the group's threads. Elsewhere in the wide stages, and in the 1536-point
+// split-precision plans, it raised ptxas's register count of the whole row kernel (1536-point
+// rows: 64 -> 100 registers, a third fewer blocks per SM), which cost more than the bank
+// conflict.
 template <int N, int B, int R, int TLB, bool INV, typename T, int OFF, bool SWZ = true>
 __device__ __forceinline__ void dit_stage_w(cx<T>* buf, const cx<T>* __restrict__ tws, int tid) {
     constexpr int SUB = B / R, NB = N / R;
