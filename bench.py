@@ -882,6 +882,13 @@ def main():
     h_psi = torch.from_numpy(psi32.copy()).pin_memory()
     o_eta = torch.empty_like(h_eta).pin_memory()
     o_psi = torch.empty_like(h_psi).pin_memory()
+    # untimed warm-up of the same loop: the first asynchronous call allocates the staging
+    # buffers, copy streams and events once per context
+    for _ in range(max(3, args.warmup)):
+        zk.zk_set_state_async(sim.ctx, h_eta, h_psi)
+        sim.step(W["dt"], 1)
+        zk.zk_get_state_async(sim.ctx, o_eta, o_psi)
+    zk.zk_io_join(sim.ctx)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
