@@ -186,13 +186,11 @@ cudaError_t launch_rows_inv_t(const cx<T>* ia, const cx<T>* ib, int nz, T scale,
 }
 template <typename T, int NZ, bool INV>
 cudaError_t launch_cols_t(cx<T>* f0, cx<T>* f1, int hx, const cx<T>* tw, cudaStream_t s) {
-    constexpr int TL = Plan<NZ>::TL;
-    const int threads = TL >= 128 ? TL : 128;
-    const int cols = threads / TL;
-    const size_t smem = (size_t)cols * line_stride(NZ) * sizeof(cx<T>);
+    constexpr int CB = cols_cb<NZ>(), threads = CB * Plan<NZ>::TL;
+    constexpr size_t smem = cols_smem_bytes<T, NZ>();
     cudaError_t e = ensure_smem((const void*)cols_kernel<T, NZ, INV>, smem);
     if (e != cudaSuccess) return e;
-    cols_kernel<T, NZ, INV><<<(hx + cols - 1) / cols, threads, smem, s>>>(f0, f1, hx, tw);
+    cols_kernel<T, NZ, INV><<<(hx + CB - 1) / CB, threads, smem, s>>>(f0, f1, hx, tw);
     return cudaGetLastError();
 }
 

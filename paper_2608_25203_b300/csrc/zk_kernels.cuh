@@ -229,36 +229,58 @@ __global__ void rows_inv_kernel(const cx<T>* __restrict__ ia, const cx<T>* __res
     }
 }
 
-// cols: in-place column transforms of `nf` compact fields [nz][hx] (forward
-// sets the z Nyquist row to zero).
+// cols: in-place column transforms of two compact fields [nz][hx] (forward sets the z Nyquist
+// row to zero). A block takes CB adjacent columns: the tiles move as [nz][CB] row segments
+// (consecutive threads on adjacent columns of one row, so every 32-byte sector is used whole),
+// each column is transformed in shared memory by its own group of TL threads. Column slots are
+// PER apart, with PER mod 16 chosen so that a half-warp's 64-bit tile accesses hit distinct banks.
+template <int NZ>
+__host__ __device__ constexpr int cols_cb() {
+    return Plan<NZ>::TL >= 32 ? 4 : 128 / Plan<NZ>::TL;
+}
+template <int NZ>
+__host__ __device__ constexpr int cols_per() {
+    return (line_stride(NZ) + 15) / 16 * 16 + (cols_cb<NZ>() >= 16 ? 1 : 16 / cols_cb<NZ>());
+}
+template <typename T, int NZ>
+__host__ __device__ constexpr size_t cols_smem_bytes() {
+    return (size_t)cols_cb<NZ>() * cols_per<NZ>() * sizeof(cx<T>);
+}
+
 template <typename T, int NZ, bool INV>
 __global__ void cols_kernel(cx<T>* f0, cx<T>* f1, int hx, const cx<T>* __restrict__ tw) {
     using P = Plan<NZ>;
     constexpr int TL = P::TL;
-    constexpr int LS = line_stride(NZ);
+    constexpr int CB = cols_cb<NZ>();
+    constexpr int PER = cols_per<NZ>();
+    constexpr int NT = CB * TL;                    // the launch uses exactly this block size
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
     const int g = threadIdx.x / TL, lt = threadIdx.x % TL;
     const int bar = 1 + (g & 7);
-    cx<T>* line = reinterpret_cast<cx<T>*>(smem_raw) + (size_t)g * LS;
-    const int c = blockIdx.x * (blockDim.x / TL) + g;
-    const bool valid = c < hx;
-    const int cc = valid ? c : 0;
+    cx<T>* line = sm + (size_t)g * PER;
+    const int c0 = blockIdx.x * CB;
     for (int f = 0; f < 2; ++f) {
         cx<T>* fp = f == 0 ? f0 : f1;
         if (!fp) continue;
         // the z Nyquist row is zero by convention; an inverse never reads it
-        for (int i = lt; i < NZ; i += TL)
-            line[pidx(i)] = (INV && i == NZ / 2) ? mk<T>(0, 0) : fp[(long long)i * hx + cc];
-        group_sync<TL>(bar);
+        for (int i = threadIdx.x; i < NZ * CB; i += NT) {
+            const int z = i / CB, cg = i - z * CB, col = c0 + cg;
+            sm[(size_t)cg * PER + pidx(z)] =
+                (col < hx && !(INV && z == NZ / 2)) ? fp[(long long)z * hx + col] : mk<T>(0, 0);
+        }
+        __syncthreads();
         P::template run<INV, T>(line, tw, lt, bar);
-        if (valid) {
-            for (int i = lt; i < NZ; i += TL) {
-                cx<T> v = line[pidx(i)];
-                if (!INV && i == NZ / 2) v = mk<T>(0, 0);
-                fp[(long long)i * hx + c] = v;
+        __syncthreads();
+        for (int i = threadIdx.x; i < NZ * CB; i += NT) {
+            const int z = i / CB, cg = i - z * CB, col = c0 + cg;
+            if (col < hx) {
+                cx<T> v = sm[(size_t)cg * PER + pidx(z)];
+                if (!INV && z == NZ / 2) v = mk<T>(0, 0);
+                fp[(long long)z * hx + col] = v;
             }
         }
-        group_sync<TL>(bar);
+        __syncthreads();
     }
 }
 

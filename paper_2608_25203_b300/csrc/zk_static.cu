@@ -240,12 +240,11 @@ cudaError_t s_rows_inv(const cx<float>* ia, int nz, float scale, float* fa, cons
 }
 template <int N, bool INV>
 cudaError_t s_cols(cx<float>* f0, cx<float>* f1, int hx, const cx<float>* tw, cudaStream_t s) {
-    constexpr int TL = Plan<N>::TL;
-    const int threads = TL >= 128 ? TL : 128, cols = threads / TL;
-    const size_t smem = (size_t)cols * line_stride(N) * sizeof(cx<float>);
+    constexpr int CB = cols_cb<N>(), threads = CB * Plan<N>::TL;
+    constexpr size_t smem = cols_smem_bytes<float, N>();
     cudaError_t e = smem_attr((const void*)cols_kernel<float, N, INV>, smem);
     if (e != cudaSuccess) return e;
-    cols_kernel<float, N, INV><<<(hx + cols - 1) / cols, threads, smem, s>>>(f0, f1, hx, tw);
+    cols_kernel<float, N, INV><<<(hx + CB - 1) / CB, threads, smem, s>>>(f0, f1, hx, tw);
     return cudaGetLastError();
 }
 
